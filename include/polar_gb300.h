@@ -1,0 +1,162 @@
+/*
+ * polar_gb300.h -- C ABI of the GB300-native hybrid BP + CA-SCL polar decoder
+ * (Cammerer, Leible, Stahl, Hoydis, ten Brink, arXiv 1609.09358).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers marked "device" must point to memory of the current CUDA device; "host" pointers
+ *     to ordinary host memory.  The caller owns every buffer.  Decoder calls never allocate: the
+ *     scratch they need comes from the caller's `workspace` (size from polar_workspace_bytes).
+ *     The library keeps one small static device table of code descriptions (POLAR_MAX_CODES
+ *     slots), filled on the first use of a code on a device.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*, NULL = legacy default
+ *     stream).  The first call with a new code uploads that code's tables with a copy on
+ *     `stream`; make it before any stream capture.
+ *   - Return value: POLAR_OK (0) or a negative POLAR_ERR_*; polar_last_error() then gives a
+ *     one-line message (thread-local).  The library never aborts the process.
+ *   - Bit vectors are packed little-endian: bit p of a row is bit (p % 8) of byte p / 8.
+ *     Rows are padded to whole bytes.
+ *   - Index conventions (Sec. II, Fig. 1): x = u G with G = F^{(x)n}, F = [[1,0],[1,1]] in
+ *     natural order (no bit reversal); information positions in ascending index order; the
+ *     payload occupies the first P = K - crc_len of them and the CRC the last crc_len.
+ *   - CRC: generator x^c + crc_poly, MSB first, register initialised to 0, no reflection, no
+ *     final XOR (e.g. 0x07 for c = 8, 0x1021 for c = 16, 0x864CFB for c = 24).
+ *   - Hard decisions are bit = (LLR < 0); frozen positions decode to 0.
+ */
+#ifndef POLAR_GB300_H
+#define POLAR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- return codes */
+#define POLAR_OK 0
+#define POLAR_ERR_ARG (-1)       /* invalid argument (sizes, pointers, code description) */
+#define POLAR_ERR_WORKSPACE (-2) /* workspace NULL or smaller than polar_workspace_bytes() */
+#define POLAR_ERR_CUDA (-3)      /* a CUDA runtime call or kernel launch failed */
+#define POLAR_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up */
+#define POLAR_ERR_CAPACITY (-5)  /* more distinct codes in use than POLAR_MAX_CODES */
+
+/* ---------------------------------------------------------------- per-frame status bytes */
+#define POLAR_FRAME_BP_OK 1        /* BP met the CRC within max_iters */
+#define POLAR_FRAME_SCL_OK 2       /* CA-SCL found a CRC-passing path */
+#define POLAR_FRAME_SCL_CRC_FAIL 3 /* CA-SCL found none; the best-metric path is output */
+#define POLAR_FRAME_BP_FAIL 4      /* bp_decode only: CRC not met after max_iters */
+
+/* ---------------------------------------------------------------- options */
+#define POLAR_FP32 0 /* BP messages in binary32 */
+#define POLAR_FP16 1 /* BP messages in binary16, two frames per half2 register */
+
+#define POLAR_OP_BP 0
+#define POLAR_OP_SCL 1
+#define POLAR_OP_HYBRID 2
+
+#define POLAR_MIN_N 128
+#define POLAR_MAX_N 2048
+#define POLAR_MAX_L 32
+#define POLAR_MAX_CODES 32
+
+/* A polar code.  N = 2^n with POLAR_MIN_N <= N <= POLAR_MAX_N; K non-frozen positions of which
+ * crc_len (0, 8, 16 or 24) carry the CRC, crc_len <= K <= N; frozen: HOST pointer to N bytes,
+ * 1 = frozen (value 0), 0 = information.  The struct and the table are read during the call
+ * only. */
+typedef struct polar_code {
+    int32_t N;
+    int32_t K;
+    int32_t crc_len;
+    uint32_t crc_poly;
+    const uint8_t* frozen;
+} polar_code;
+
+/* Frozen-set construction (Sec. II: information on the K most reliable bit-channels; Sec. II-A
+ * names the Bhattacharyya parameter as the reliability measure).  Host only, FP64, log domain:
+ * ln Z0 = -design_rate * 10^(design_ebn0_db / 10); index bits are read MSB first, a 0 bit maps
+ * Z -> 2Z - Z^2 and a 1 bit Z -> Z^2; the K indices with the smallest Z (ties: larger index) are
+ * information positions.  frozen_out: host, N bytes; info_idx_out: host, K int32 ascending (may
+ * be NULL).  Errors: POLAR_ERR_ARG for N not a power of two in [2, 2^20], K outside [0, N] or
+ * design_rate <= 0. */
+int polar_construct(int32_t N, int32_t K, double design_ebn0_db, double design_rate,
+                    uint8_t* frozen_out, int32_t* info_idx_out);
+
+/* Systematic CRC + polar encoder (Sec. II, x = u G; CRC-aided construction of Sec. II-A).
+ * payload: device, [B][ceil(P/8)] packed payload bits; codeword: device, [B][N/8] packed code
+ * bits.  B >= 0 (B = 0 is a no-op). */
+int polar_encode(const polar_code* code, const uint8_t* payload, int32_t B, uint8_t* codeword,
+                 void* stream);
+
+/* Seeded workload generator (not part of the paper's method): payload bits and BPSK-over-AWGN
+ * channel LLRs from the counter-based generator Philox4x32-10 (Salmon et al., SC'11).  Key =
+ * (seed low, seed high); counter = (block, frame low, stream, frame high) for frame index
+ * frame0 + b.  polar_random_payload: stream 0, bit p of a frame is bit p % 32 of word p / 32.
+ * polar_awgn_llr: stream 1, Box-Muller on 24-bit uniforms; llr = 2 (1 - 2x + sigma z) / sigma^2
+ * (the LLR definition of Sec. II-A).  payload: device [B][ceil(P/8)]; codeword: device [B][N/8]
+ * packed; llr: device float [B][N]. */
+int polar_random_payload(int32_t B, int32_t P, uint64_t seed, uint64_t frame0, uint8_t* payload,
+                         void* stream);
+int polar_awgn_llr(const uint8_t* codeword, int32_t B, int32_t N, float sigma, uint64_t seed,
+                   uint64_t frame0, float* llr, void* stream);
+
+/* Min-sum belief propagation with CRC early stop (Sec. II-B; PE of Fig. 2 on the graph of
+ * Fig. 1).  One iteration updates the R messages of columns 2..n+1, then the L messages of
+ * columns n..1, each PE computing
+ *   R_out1 = g(R_in1, L_in2 + R_in2), R_out2 = g(R_in1, L_in1) + R_in2,
+ *   L_out1 = g(L_in1, L_in2 + R_in2), L_out2 = g(R_in1, L_in1) + L_in2,
+ * g(a, b) = sign(a) sign(b) min(|a|, |b|); every message and the channel LLRs are clipped to
+ * [-llr_max, llr_max] (NaN channel values read as 0).  Init L_{i,n+1} = LLR(y_i),
+ * R_{i,1} = llr_max f_i.  After each iteration the hard decision of LLR(u_i) = L_{i,1} + R_{i,1}
+ * is CRC-checked and the frame stops when it passes.
+ *   llr: device float [B][N].  max_iters >= 1.  llr_max > 0.
+ *   precision: POLAR_FP32 (bit-exact with a binary32 reference) or POLAR_FP16 (binary16
+ *     messages, llr_max <= 32768).
+ *   wms_scales: NULL, or device float [wms_iters][2][n][N] learned weights of a weighted
+ *     min-sum BP: entry [t][0][s-1][i] scales the g term of the R message leaving PE stage s at
+ *     node i in iteration t, entry [t][1][s-1][i] that of the L message; iterations
+ *     t >= wms_iters run unweighted.
+ *   bits: device [B][ceil(P/8)] decided payload.  status: device [B] POLAR_FRAME_BP_OK or
+ *     POLAR_FRAME_BP_FAIL.  iters: device uint16 [B], iterations run.
+ *   llr_u, llr_x: NULL or device float [B][N], the final LLR(u) and LLR(x).
+ *   workspace: may be NULL (polar_workspace_bytes(.., POLAR_OP_BP) is 0). */
+int bp_decode(const polar_code* code, const float* llr, int32_t B, int32_t max_iters,
+              float llr_max, int32_t precision, const float* wms_scales, int32_t wms_iters,
+              uint8_t* bits, uint8_t* status, uint16_t* iters, float* llr_u, float* llr_x,
+              void* workspace, size_t ws_bytes, void* stream);
+
+/* CRC-aided successive cancellation list decoding (Sec. II-A; list decoding of Tal and Vardy).
+ * Min-sum f, exact g, path metric m' = m + |lambda| [b != HD(lambda)]; at an information bit the
+ * L smallest of the 2L candidates by (m', 2 path + b) survive (the paper's pruned pseudo sort
+ * with a total order) and are renumbered in ascending candidate index; after the last bit the
+ * first path, in (metric, path index) order, whose CRC passes is output.
+ *   llr: device float [B][N].  L in {1, 2, 4, 8, 16, 32}.
+ *   bits: device [B][ceil(P/8)]; status: device [B] POLAR_FRAME_SCL_OK / _SCL_CRC_FAIL.
+ *   workspace: device, >= polar_workspace_bytes(code, B, L, POLAR_OP_SCL) bytes. */
+int scl_decode(const polar_code* code, const float* llr, int32_t B, int32_t L, uint8_t* bits,
+               uint8_t* status, void* workspace, size_t ws_bytes, void* stream);
+
+/* Hybrid decoder (Sec. III, Fig. 3): BP as in bp_decode on every frame; the frames whose CRC
+ * still fails after max_iters are compacted on the device and decoded by CA-SCL as in
+ * scl_decode.  status: POLAR_FRAME_BP_OK, _SCL_OK or _SCL_CRC_FAIL; iters: BP iterations.
+ *   workspace: device, >= polar_workspace_bytes(code, B, L, POLAR_OP_HYBRID) bytes. */
+int hybrid_decode(const polar_code* code, const float* llr, int32_t B, int32_t max_iters,
+                  float llr_max, int32_t precision, const float* wms_scales, int32_t wms_iters,
+                  int32_t L, uint8_t* bits, uint8_t* status, uint16_t* iters, void* workspace,
+                  size_t ws_bytes, void* stream);
+
+/* Device workspace needed by an operation (op = POLAR_OP_*) on B frames with list size L
+ * (ignored for POLAR_OP_BP).  Returns 0 on invalid arguments as well as when none is needed. */
+size_t polar_workspace_bytes(const polar_code* code, int32_t B, int32_t L, int32_t op);
+
+/* Number of frames that the last hybrid_decode on `workspace` sent to CA-SCL, copied to *out
+ * (host) after synchronising `stream`. */
+int polar_hybrid_fallback_count(const void* workspace, int32_t* out, void* stream);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* polar_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLAR_GB300_H */

@@ -178,7 +178,8 @@ void or_build_u(const unsigned char* payload, int N, int K, const int* info_idx,
     for (int k = 0; k < c; ++k) u[info_idx[P + k]] = crc[k];
 }
 
-/* Batch encoder: payload [B][P] (one byte per bit) -> codeword [B][N] (one byte per bit). */
+/* Batch encoder: payload [B][P] (one byte per bit) -> codeword [B][N] (one byte per bit), by the
+ * Fig. 1 circuit (pinned equal to the matrix definition). */
 void or_encode_batch(const unsigned char* payload, int B, int N, int K, const int* info_idx,
                      unsigned poly, int c, unsigned char* x)
 {
@@ -186,7 +187,7 @@ void or_encode_batch(const unsigned char* payload, int B, int N, int K, const in
     unsigned char* u = (unsigned char*)malloc((size_t)N);
     for (int b = 0; b < B; ++b) {
         or_build_u(payload + (size_t)b * P, N, K, info_idx, poly, c, u);
-        or_polar_transform(u, N, x + (size_t)b * N);
+        or_encode_circuit(u, N, x + (size_t)b * N);
     }
     free(u);
 }

@@ -1,0 +1,239 @@
+"""Thin ctypes binding of the C ABI in include/polar_gb300.h (same names, argument marshalling only).
+
+Device buffers are torch CUDA tensors; every call is queued on the current torch stream.  All
+decoding runs in the CUDA kernels of libpolar_gb300.so: if the library is missing, the first call
+raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpolar_gb300.so")
+
+POLAR_OK = 0
+POLAR_FP32, POLAR_FP16 = 0, 1
+POLAR_OP_BP, POLAR_OP_SCL, POLAR_OP_HYBRID = 0, 1, 2
+FRAME_BP_OK, FRAME_SCL_OK, FRAME_SCL_CRC_FAIL, FRAME_BP_FAIL = 1, 2, 3, 4
+CRC_POLYS = {0: 0x0, 8: 0x07, 16: 0x1021, 24: 0x864CFB}
+
+_lib = None
+
+
+class PolarError(RuntimeError):
+    pass
+
+
+class _PolarCode(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("K", ctypes.c_int32), ("crc_len", ctypes.c_int32),
+                ("crc_poly", ctypes.c_uint32), ("frozen", ctypes.POINTER(ctypes.c_uint8))]
+
+
+_vp, _i32, _u64, _f32, _f64, _sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_float,
+                                    ctypes.c_double, ctypes.c_size_t)
+_CP = ctypes.POINTER(_PolarCode)
+
+# name -> (restype, argtypes); every exported symbol of the header
+SIGNATURES = {
+    "polar_construct": (ctypes.c_int, [_i32, _i32, _f64, _f64, _vp, _vp]),
+    "polar_encode": (ctypes.c_int, [_CP, _vp, _i32, _vp, _vp]),
+    "polar_random_payload": (ctypes.c_int, [_i32, _i32, _u64, _u64, _vp, _vp]),
+    "polar_awgn_llr": (ctypes.c_int, [_vp, _i32, _i32, _f32, _u64, _u64, _vp, _vp]),
+    "bp_decode": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
+                                 _vp]),
+    "scl_decode": (ctypes.c_int, [_CP, _vp, _i32, _i32, _vp, _vp, _vp, _sz, _vp]),
+    "hybrid_decode": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _i32, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _sz,
+                                     _vp]),
+    "polar_workspace_bytes": (_sz, [_CP, _i32, _i32, _i32]),
+    "polar_hybrid_fallback_count": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), _vp]),
+    "polar_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Open the library (built by paper_1609_09358_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise PolarError("libpolar_gb300.so not built (%s): run paper_1609_09358_gb300/build.py" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != POLAR_OK:
+        raise PolarError("%s failed (%d): %s" % (what, rc, load().polar_last_error().decode()))
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise PolarError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise PolarError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+@dataclass
+class PolarCode:
+    """Host description of a code; `frozen` is uint8 [N] (1 = frozen)."""
+    N: int
+    K: int
+    crc_len: int
+    frozen: np.ndarray
+    crc_poly: int = -1
+    _c: _PolarCode = field(default=None, repr=False)
+
+    def __post_init__(self):
+        if self.crc_poly < 0:
+            self.crc_poly = CRC_POLYS[self.crc_len]
+        self.frozen = np.ascontiguousarray(self.frozen, dtype=np.uint8)
+        self._c = _PolarCode(self.N, self.K, self.crc_len, self.crc_poly,
+                             self.frozen.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+
+    @property
+    def P(self) -> int:
+        return self.K - self.crc_len
+
+    @property
+    def n(self) -> int:
+        return self.N.bit_length() - 1
+
+    @property
+    def row_bytes(self) -> int:
+        return (self.P + 7) // 8
+
+    @property
+    def info_idx(self) -> np.ndarray:
+        return np.nonzero(self.frozen == 0)[0].astype(np.int32)
+
+    def ref(self):
+        return ctypes.byref(self._c)
+
+
+def polar_construct(N: int, K: int, design_ebn0_db: float, design_rate: float):
+    frozen = np.zeros(N, np.uint8)
+    info = np.zeros(max(K, 1), np.int32)
+    _check(load().polar_construct(N, K, design_ebn0_db, design_rate, frozen.ctypes.data, info.ctypes.data),
+           "polar_construct")
+    return frozen, info[:K]
+
+
+def make_code(N: int, K: int, crc_len: int, design_ebn0_db: float = 0.0, design_rate=None) -> PolarCode:
+    """Bhattacharyya construction at the design point (design rate defaults to the payload rate)."""
+    if design_rate is None:
+        design_rate = (K - crc_len) / N
+    frozen, _ = polar_construct(N, K, design_ebn0_db, design_rate)
+    return PolarCode(N, K, crc_len, frozen)
+
+
+def polar_encode(code: PolarCode, payload, codeword, stream=None) -> None:
+    B = payload.shape[0]
+    _check(load().polar_encode(code.ref(), _ptr(payload), B, _ptr(codeword), _stream(stream)), "polar_encode")
+
+
+def polar_random_payload(B: int, P: int, seed: int, frame0: int, payload, stream=None) -> None:
+    _check(load().polar_random_payload(B, P, seed, frame0, _ptr(payload), _stream(stream)),
+           "polar_random_payload")
+
+
+def polar_awgn_llr(codeword, N: int, sigma: float, seed: int, frame0: int, llr, stream=None) -> None:
+    B = codeword.shape[0]
+    _check(load().polar_awgn_llr(_ptr(codeword), B, N, sigma, seed, frame0, _ptr(llr), _stream(stream)),
+           "polar_awgn_llr")
+
+
+def polar_workspace_bytes(code: PolarCode, B: int, L: int, op: int) -> int:
+    return int(load().polar_workspace_bytes(code.ref(), B, L, op))
+
+
+def bp_decode(code: PolarCode, llr, max_iters: int, llr_max: float, precision: int, wms_scales, bits, status,
+              iters, llr_u=None, llr_x=None, workspace=None, stream=None) -> None:
+    B = llr.shape[0]
+    w_iters = 0 if wms_scales is None else int(wms_scales.shape[0])
+    ws_b = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load().bp_decode(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, _ptr(wms_scales), w_iters,
+                            _ptr(bits), _ptr(status), _ptr(iters), _ptr(llr_u), _ptr(llr_x), _ptr(workspace), ws_b,
+                            _stream(stream)), "bp_decode")
+
+
+def scl_decode(code: PolarCode, llr, L: int, bits, status, workspace, stream=None) -> None:
+    B = llr.shape[0]
+    ws_b = workspace.numel() * workspace.element_size()
+    _check(load().scl_decode(code.ref(), _ptr(llr), B, L, _ptr(bits), _ptr(status), _ptr(workspace), ws_b,
+                             _stream(stream)), "scl_decode")
+
+
+def hybrid_decode(code: PolarCode, llr, max_iters: int, llr_max: float, precision: int, wms_scales, L: int, bits,
+                  status, iters, workspace, stream=None) -> None:
+    B = llr.shape[0]
+    w_iters = 0 if wms_scales is None else int(wms_scales.shape[0])
+    ws_b = workspace.numel() * workspace.element_size()
+    _check(load().hybrid_decode(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, _ptr(wms_scales), w_iters,
+                                L, _ptr(bits), _ptr(status), _ptr(iters), _ptr(workspace), ws_b, _stream(stream)),
+           "hybrid_decode")
+
+
+def polar_hybrid_fallback_count(workspace, stream=None) -> int:
+    out = _i32(0)
+    _check(load().polar_hybrid_fallback_count(_ptr(workspace), ctypes.byref(out), _stream(stream)),
+           "polar_hybrid_fallback_count")
+    return int(out.value)
+
+
+# ------------------------------------------------------------------------ convenience wrappers
+class Decoder:
+    """Owns the output and workspace tensors for one code and batch size (device memory via torch)."""
+
+    def __init__(self, code: PolarCode, B: int, L: int = 8, device="cuda"):
+        import torch
+        self.code, self.B, self.L = code, B, L
+        self.bits = torch.zeros((B, code.row_bytes), dtype=torch.uint8, device=device)
+        self.status = torch.zeros(B, dtype=torch.uint8, device=device)
+        self.iters = torch.zeros(B, dtype=torch.int16, device=device)
+        ws = max(polar_workspace_bytes(code, B, L, POLAR_OP_HYBRID), polar_workspace_bytes(code, B, L, POLAR_OP_SCL))
+        self.workspace = torch.zeros(max(ws, 256), dtype=torch.uint8, device=device)
+
+    def hybrid(self, llr, max_iters: int, llr_max: float = 20.0, precision: int = POLAR_FP32, wms_scales=None,
+               stream=None):
+        hybrid_decode(self.code, llr, max_iters, llr_max, precision, wms_scales, self.L, self.bits, self.status,
+                      self.iters, self.workspace, stream)
+        return self.bits, self.status, self.iters
+
+    def bp(self, llr, max_iters: int, llr_max: float = 20.0, precision: int = POLAR_FP32, wms_scales=None,
+           llr_u=None, llr_x=None, stream=None):
+        bp_decode(self.code, llr, max_iters, llr_max, precision, wms_scales, self.bits, self.status, self.iters,
+                  llr_u, llr_x, None, stream)
+        return self.bits, self.status, self.iters
+
+    def scl(self, llr, stream=None):
+        scl_decode(self.code, llr, self.L, self.bits, self.status, self.workspace, stream)
+        return self.bits, self.status
+
+
+def unpack_bits(packed: np.ndarray, nbits: int) -> np.ndarray:
+    """[B][ceil(nbits/8)] little-endian packed bytes -> uint8 [B][nbits], one byte per bit."""
+    packed = np.asarray(packed, dtype=np.uint8).reshape(packed.shape[0], -1)
+    return np.unpackbits(packed, axis=1, bitorder="little")[:, :nbits]
+
+
+def pack_bits(bits: np.ndarray) -> np.ndarray:
+    """uint8 [B][nbits] (one byte per bit) -> [B][ceil(nbits/8)] little-endian packed bytes."""
+    bits = np.asarray(bits, dtype=np.uint8)
+    return np.packbits(bits, axis=1, bitorder="little")

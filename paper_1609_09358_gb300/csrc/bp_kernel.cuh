@@ -1,0 +1,418 @@
+// bp_kernel.cuh -- min-sum belief propagation with CRC early stop (Sec. II-B of the paper),
+// register-blocked for sm_103a.
+//
+// Graph (Fig. 1, PE of Fig. 2): columns s = 1..n+1 (u side .. channel side); the PE of stage s
+// joins nodes j and j + 2^(s-1) (bit s-1 of j clear).  One iteration runs the R sweep over
+// stages 1..n and then the L sweep over stages n..1:
+//   R sweep:  R[s+1][j]   = g(R[s][j], L[s+1][j+d] + R[s][j+d])
+//             R[s+1][j+d] = g(R[s][j], L[s+1][j])   + R[s][j+d]
+//   L sweep:  L[s][j]     = g(L[s+1][j], L[s+1][j+d] + R[s][j+d])
+//             L[s][j+d]   = g(R[s][j], L[s+1][j])   + L[s+1][j+d]
+// every result clipped to [-M, M]; g is min-sum.  After the L sweep the hard decision of
+// L[1][i] + R[1][i] is CRC-checked and the frame stops when the syndrome is zero.
+//
+// Execution plan (own design, not the paper's one-thread-per-PE layout): a frame is decoded by
+// T = N / 2^b threads, each owning 2^b nodes of every column.  The n index bits are cut into
+// groups of b consecutive bits; while the sweep is inside group g, a thread's 2^b nodes differ
+// exactly in the bits of g's window, so b consecutive PE stages run entirely in registers.  At
+// a group boundary the boundary column is exchanged once through a swizzled shared-memory
+// buffer (bank-conflict free for every access of every plan, checked at compile time).  All
+// messages of all columns stay in registers for the frame's whole life; HBM is touched once to
+// read the channel LLRs and once to write the decided payload bits.
+//
+// Storage of column c: R[c] lives in the mapping of stage c (the group that reads it), L[c] in
+// the mapping of stage c-1.  The clip of g(R[s][j], .) and g(L[s+1][j], .) is skipped when no
+// learned weight scales it: |g(a, b)| <= |a| <= M already.
+#pragma once
+
+#include <type_traits>
+#include <utility>
+
+#include "polar_common.cuh"
+
+namespace polar {
+
+template <int I, int E, class Fn>
+__device__ __forceinline__ void static_for(Fn&& fn)
+{
+    if constexpr (I < E) {
+        fn(std::integral_constant<int, I>{});
+        static_for<I + 1, E>(fn);
+    }
+}
+
+template <int I, int E, class Fn>  // I, I-1, ..., E
+__device__ __forceinline__ void static_for_down(Fn&& fn)
+{
+    if constexpr (I >= E) {
+        fn(std::integral_constant<int, I>{});
+        static_for_down<I - 1, E>(fn);
+    }
+}
+
+template <int LOGN_, int LOGR_>
+struct BPPlan {
+    static constexpr int LOGN = LOGN_, LOGR = LOGR_;
+    static constexpr int N = 1 << LOGN, R = 1 << LOGR, T = N >> LOGR;
+    static constexpr int NG = (LOGN + LOGR - 1) / LOGR;
+    static constexpr int NW = (T + 31) / 32;
+    // group of the PE stage with index bit q (stage s = q + 1)
+    __host__ __device__ static constexpr int grp(int q) { return q / LOGR; }
+    // first index bit of group g's register window (the last window is pulled down to fit)
+    __host__ __device__ static constexpr int win(int g) { return (g + 1) * LOGR <= LOGN ? g * LOGR : LOGN - LOGR; }
+    // node held in register k by thread t while in group g
+    __host__ __device__ static constexpr int node(int g, int t, int k)
+    {
+        return (t & ((1 << win(g)) - 1)) | (k << win(g)) | ((t >> win(g)) << (win(g) + LOGR));
+    }
+    // column exchanges: the R sweep leaving stage s crosses into another group, or the L sweep
+    // leaving stage s does; xidx numbers the exchanges of one iteration in execution order
+    __host__ __device__ static constexpr bool rcross(int s) { return s < LOGN && grp(s) != grp(s - 1); }
+    __host__ __device__ static constexpr bool lcross(int s) { return s > 1 && grp(s - 2) != grp(s - 1); }
+    __host__ __device__ static constexpr int xidx_r(int s)
+    {
+        int c = 0;
+        for (int i = 1; i < s; ++i) c += rcross(i);
+        return c;
+    }
+    __host__ __device__ static constexpr int xidx_l(int s)
+    {
+        int c = xidx_r(LOGN + 1);
+        for (int i = LOGN; i > s; --i) c += lcross(i);
+        return c;
+    }
+    // shared-memory address of node j in the exchange buffer: XOR of index bits 5..7 into the
+    // bank bits, chosen so that every warp access of every group hits 32 distinct banks.
+    __host__ __device__ static constexpr int swz(int j)
+    {
+        if constexpr (LOGR == 3)
+            return j ^ (((j >> 5) & 1) * 1) ^ (((j >> 6) & 1) * 10) ^ (((j >> 7) & 1) * 20);
+        else
+            return j ^ (((j >> 5) & 1) * 5) ^ (((j >> 6) & 1) * 26);
+    }
+};
+
+template <class P>
+constexpr bool plan_is_conflict_free()
+{
+    for (int g = 0; g < P::NG; ++g)
+        for (int k = 0; k < P::R; ++k)
+            for (int w = 0; w < P::NW; ++w) {
+                uint32_t seen = 0;
+                for (int l = 0; l < 32 && w * 32 + l < P::T; ++l) {
+                    const int a = P::swz(P::node(g, w * 32 + l, k));
+                    if (a < 0 || a >= P::N) return false;
+                    const uint32_t bit = 1u << (a & 31);
+                    if (seen & bit) return false;
+                    seen |= bit;
+                }
+            }
+    // every node owned exactly once per group
+    for (int g = 0; g < P::NG; ++g) {
+        int sum = 0;
+        for (int t = 0; t < P::T; ++t)
+            for (int k = 0; k < P::R; ++k) sum += P::node(g, t, k);
+        if (sum != P::N * (P::N - 1) / 2) return false;
+    }
+    return true;
+}
+
+struct BPArgs {
+    const float* llr;
+    int B;
+    int max_iters;
+    float llr_max;
+    const float* w;  // learned weights [w_iters][2][n][N] or null
+    int w_iters;
+    uint8_t* bits;
+    uint8_t* status;
+    uint16_t* iters;
+    float* llr_u;
+    float* llr_x;
+    const DevCode* code;
+    int* fail_count;  // hybrid: compaction of the CRC-failed frames (null for bp_decode)
+    int* fail_list;
+    int row_bytes;
+};
+
+// Message traits: FP32 (one frame per thread) or half2 (two frames per thread).
+template <class MSG>
+struct MsgTraits;
+template <>
+struct MsgTraits<float> {
+    static constexpr int FPT = 1;
+    __device__ static float splat(float v) { return v; }
+    __device__ static float load2(const float* a, const float* b, int j, float m)
+    {
+        return stage_clip(__ldg(a + j), m);
+    }
+    __device__ static bool neg(float v, int h) { return v < 0.0f; }
+    __device__ static float to_f(float v, int h) { return v; }
+};
+template <>
+struct MsgTraits<__half2> {
+    static constexpr int FPT = 2;
+    __device__ static __half2 splat(float v) { return __float2half2_rn(v); }
+    __device__ static __half2 load2(const float* a, const float* b, int j, float m)
+    {
+        const float x = stage_clip(__ldg(a + j), m);
+        const float y = b ? stage_clip(__ldg(b + j), m) : 0.0f;
+        return __floats2half2_rn(x, y);
+    }
+    __device__ static bool neg(__half2 v, int h)
+    {
+        return __hlt(h ? __high2half(v) : __low2half(v), __float2half(0.0f));
+    }
+    __device__ static float to_f(__half2 v, int h) { return __half2float(h ? __high2half(v) : __low2half(v)); }
+};
+
+template <int LOGN>
+struct BPConfig;  // thread plan and frames (or frame pairs) per CTA for each block length
+template <> struct BPConfig<7>  { using Plan = BPPlan<7, 2>;  static constexpr int F = 4; };
+template <> struct BPConfig<8>  { using Plan = BPPlan<8, 3>;  static constexpr int F = 4; };
+template <> struct BPConfig<9>  { using Plan = BPPlan<9, 3>;  static constexpr int F = 1; };
+template <> struct BPConfig<10> { using Plan = BPPlan<10, 3>; static constexpr int F = 1; };
+template <> struct BPConfig<11> { using Plan = BPPlan<11, 3>; static constexpr int F = 1; };
+
+template <class P>
+__host__ __device__ constexpr int bp_slot_words()
+{
+    // exchange buffer [2][N] | syndrome columns, thread-major [R][T] | partial syndromes
+    // [2][2][NW] | packed payload bits [2][N/32]
+    return 2 * P::N + P::N + 4 * P::NW + 2 * (P::N / 32);
+}
+
+// THREADS = F * T (passed explicitly: launch bounds take no dependent member expression)
+template <int LOGN, class MSG, bool WEIGHTED, int THREADS>
+__global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
+{
+    using P = typename BPConfig<LOGN>::Plan;
+    using MT = MsgTraits<MSG>;
+    constexpr int F = BPConfig<LOGN>::F;
+    constexpr int N = P::N, R = P::R, T = P::T, NG = P::NG, NW = P::NW, n = LOGN;
+    constexpr int FPT = MT::FPT;
+    constexpr int SW = bp_slot_words<P>();
+    static_assert(THREADS == F * T, "launch shape");
+    static_assert(T <= 32 || F == 1, "frame groups wider than a warp own their CTA");
+    static_assert(plan_is_conflict_free<P>(), "exchange layout has bank conflicts");
+    // exchanges alternate between the two buffers; an even count per iteration keeps the
+    // alternation across iterations, so a buffer is rewritten only after a barrier that follows
+    // every read of its previous contents
+    static_assert(P::xidx_l(0) % 2 == 0, "odd number of exchanges per iteration");
+
+    extern __shared__ uint32_t smem[];
+    const int slot = threadIdx.x / T;
+    const int t = threadIdx.x % T;
+    const int frame0 = (blockIdx.x * F + slot) * FPT;  // first frame of this thread group
+    if (frame0 >= a.B) return;  // whole frame groups leave together
+    const bool has1 = FPT == 2 && frame0 + 1 < a.B;
+
+    MSG* xbuf = reinterpret_cast<MSG*>(smem + slot * SW);  // [2][N]; half2 uses the first half
+    uint32_t* csyn = smem + slot * SW + 2 * N;             // [R][T]
+    uint32_t* synp = csyn + N;                             // [2 parity][2 frame][NW]
+    uint32_t* pbits = synp + 4 * NW;                       // [2 frame][N/32]
+    const DevCode& C = *a.code;
+    const float M = a.llr_max;
+    const MSG Mv = MT::splat(M);
+
+    MSG Lc[n + 2][R];
+    MSG Rc[n + 2][R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int j = P::node(0, t, k);
+        csyn[k * T + t] = C.colsyn[j];
+        Rc[1][k] = frozen_at(C.frozen_bits, j) ? Mv : MT::splat(0.0f);
+    }
+    {
+        const float* y0 = a.llr + (size_t)frame0 * N;
+        const float* y1 = has1 ? y0 + N : nullptr;
+#pragma unroll
+        for (int k = 0; k < R; ++k) Lc[n + 1][k] = MT::load2(y0, y1, P::node(NG - 1, t, k), M);
+    }
+#pragma unroll
+    for (int c = 2; c <= n; ++c)
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            Lc[c][k] = MT::splat(0.0f);
+            Rc[c][k] = MT::splat(0.0f);
+        }
+
+    auto weight = [&](int it, int dir, int s, int j) -> MSG {
+        return MT::splat(__ldg(a.w + (((size_t)it * 2 + dir) * n + (s - 1)) * N + j));
+    };
+
+    // write the decided payload bits, status and optional LLRs of frame half h after `it_done`
+    // iterations; called uniformly by the T threads of the frame group
+    auto finalize = [&](int h, int it_done, bool ok) {
+        const int frame = frame0 + h;
+        uint32_t* pb = pbits + h * (N / 32);
+        for (int i = t; i < N / 32; i += T) pb[i] = 0u;
+        frame_sync<T>(slot);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int j = P::node(0, t, k);
+            const int pos = C.paypos[j];
+            if (pos >= 0 && MT::neg(fadd(Lc[1][k], Rc[1][k]), h)) atomicOr(&pb[pos >> 5], 1u << (pos & 31));
+        }
+        frame_sync<T>(slot);
+        const uint8_t* pbb = reinterpret_cast<const uint8_t*>(pb);
+        uint8_t* out = a.bits + (size_t)frame * a.row_bytes;
+        for (int i = t; i < a.row_bytes; i += T) out[i] = pbb[i];
+        if (t == 0) {
+            a.iters[frame] = (uint16_t)it_done;
+            a.status[frame] = ok ? POLAR_FRAME_BP_OK : POLAR_FRAME_BP_FAIL;
+            if (!ok && a.fail_list) a.fail_list[atomicAdd(a.fail_count, 1)] = frame;
+        }
+        if (a.llr_u) {
+#pragma unroll
+            for (int k = 0; k < R; ++k)
+                a.llr_u[(size_t)frame * N + P::node(0, t, k)] = MT::to_f(fadd(Lc[1][k], Rc[1][k]), h);
+        }
+        if (a.llr_x) {
+            // R[n+1] of the last R sweep, recomputed from R[n] and the channel column
+            constexpr int q = n - 1, g = P::grp(q), dd = 1 << (q - P::win(g));
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                if (k & dd) continue;
+                const int k2 = k | dd;
+                MSG o1 = xmin(Rc[n][k], fadd(Lc[n + 1][k2], Rc[n][k2]));
+                MSG gg = xmin(Rc[n][k], Lc[n + 1][k]);
+                if constexpr (WEIGHTED) {
+                    if (it_done - 1 < a.w_iters) {
+                        o1 = clipm(fmul(weight(it_done - 1, 0, n, P::node(g, t, k)), o1), Mv);
+                        gg = fmul(weight(it_done - 1, 0, n, P::node(g, t, k2)), gg);
+                    }
+                }
+                const MSG o2 = clipm(fadd(gg, Rc[n][k2]), Mv);
+                a.llr_x[(size_t)frame * N + P::node(g, t, k)] = MT::to_f(fadd(Lc[n + 1][k], o1), h);
+                a.llr_x[(size_t)frame * N + P::node(g, t, k2)] = MT::to_f(fadd(Lc[n + 1][k2], o2), h);
+            }
+        }
+    };
+
+    bool done0 = false, done1 = !has1 && FPT == 2;
+    int it = 0;
+    while (it < a.max_iters) {
+        const bool wt = WEIGHTED && it < a.w_iters;
+        // ------------------------------------------------------------------ R sweep
+        static_for<1, n + 1>([&](auto S) {
+            constexpr int s = S.value, q = s - 1, g = P::grp(q), dd = 1 << (q - P::win(g));
+            constexpr bool last = s == n;
+            constexpr bool cross = P::rcross(s);
+            MSG* xb = xbuf + (P::xidx_r(s) & 1) * N;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                if (k & dd) continue;
+                const int k2 = k | dd;
+                const MSG a1 = Rc[s][k], a2 = Rc[s][k2], l1 = Lc[s + 1][k], l2 = Lc[s + 1][k2];
+                MSG o1 = xmin(a1, fadd(l2, a2));
+                MSG gg = xmin(a1, l1);
+                if constexpr (WEIGHTED) {
+                    if (wt) {
+                        o1 = clipm(fmul(weight(it, 0, s, P::node(g, t, k)), o1), Mv);
+                        gg = fmul(weight(it, 0, s, P::node(g, t, k2)), gg);
+                    }
+                }
+                const MSG o2 = clipm(fadd(gg, a2), Mv);
+                if constexpr (!last) {
+                    if constexpr (cross) {
+                        xb[P::swz(P::node(g, t, k))] = o1;
+                        xb[P::swz(P::node(g, t, k2))] = o2;
+                    } else {
+                        Rc[s + 1][k] = o1;
+                        Rc[s + 1][k2] = o2;
+                    }
+                }
+            }
+            if constexpr (cross) {
+                frame_sync<T>(slot);
+#pragma unroll
+                for (int k = 0; k < R; ++k) Rc[s + 1][k] = xb[P::swz(P::node(P::grp(s), t, k))];
+            }
+        });
+        // ------------------------------------------------------------------ L sweep
+        uint32_t syn0 = 0, syn1 = 0;
+        static_for_down<n, 1>([&](auto S) {
+            constexpr int s = S.value, q = s - 1, g = P::grp(q), dd = 1 << (q - P::win(g));
+            constexpr bool first = s == 1;
+            constexpr bool cross = P::lcross(s);
+            MSG* xb = xbuf + (P::xidx_l(s) & 1) * N;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                if (k & dd) continue;
+                const int k2 = k | dd;
+                const MSG a1 = Rc[s][k], a2 = Rc[s][k2], l1 = Lc[s + 1][k], l2 = Lc[s + 1][k2];
+                MSG o1 = xmin(l1, fadd(l2, a2));
+                MSG gg = xmin(a1, l1);
+                if constexpr (WEIGHTED) {
+                    if (wt) {
+                        o1 = clipm(fmul(weight(it, 1, s, P::node(g, t, k)), o1), Mv);
+                        gg = fmul(weight(it, 1, s, P::node(g, t, k2)), gg);
+                    }
+                }
+                const MSG o2 = clipm(fadd(gg, l2), Mv);
+                if constexpr (cross) {
+                    xb[P::swz(P::node(g, t, k))] = o1;
+                    xb[P::swz(P::node(g, t, k2))] = o2;
+                } else {
+                    Lc[s][k] = o1;
+                    Lc[s][k2] = o2;
+                }
+            }
+            if constexpr (cross) {
+                frame_sync<T>(slot);
+#pragma unroll
+                for (int k = 0; k < R; ++k) Lc[s][k] = xb[P::swz(P::node(P::grp(s - 2), t, k))];
+            }
+            if constexpr (first) {
+                // hard decision of LLR(u) = L[1] + R[1]; XOR of the syndrome columns of the
+                // information nodes decided 1 (frozen nodes have column 0)
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const MSG u = fadd(Lc[1][k], Rc[1][k]);
+                    const uint32_t col = csyn[k * T + t];
+                    syn0 ^= MT::neg(u, 0) ? col : 0u;
+                    if constexpr (FPT == 2) syn1 ^= MT::neg(u, 1) ? col : 0u;
+                }
+            }
+        });
+        // ------------------------------------------------------------------ CRC early stop
+        syn0 = __reduce_xor_sync(0xffffffffu, syn0);
+        if constexpr (FPT == 2) syn1 = __reduce_xor_sync(0xffffffffu, syn1);
+        if constexpr (NW > 1) {
+            uint32_t* sp = synp + (it & 1) * 2 * NW;
+            if ((t & 31) == 0) {
+                sp[t >> 5] = syn0;
+                if constexpr (FPT == 2) sp[NW + (t >> 5)] = syn1;
+            }
+            frame_sync<T>(slot);
+            syn0 = 0;
+            syn1 = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                syn0 ^= sp[w];
+                if constexpr (FPT == 2) syn1 ^= sp[NW + w];
+            }
+        }
+        ++it;
+        if (!done0 && syn0 == 0) {
+            done0 = true;
+            finalize(0, it, true);
+        }
+        if constexpr (FPT == 2) {
+            if (!done1 && syn1 == 0) {
+                done1 = true;
+                finalize(1, it, true);
+            }
+            if (done0 && done1) break;
+        } else {
+            if (done0) break;
+        }
+    }
+    if (!done0) finalize(0, it, false);
+    if constexpr (FPT == 2) {
+        if (!done1) finalize(1, it, false);
+    }
+}
+
+}  // namespace polar

@@ -1,0 +1,456 @@
+// polar_api.cu -- the C ABI of include/polar_gb300.h: argument checks, the per-device code-table
+// cache, workspace layout and kernel dispatch.  Every decoding step runs in the kernels of
+// bp_kernel.cuh, scl_kernel.cuh and encode_kernels.cuh; nothing here touches frame data.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bp_kernel.cuh"
+#include "encode_kernels.cuh"
+#include "polar_common.cuh"
+#include "scl_kernel.cuh"
+
+namespace polar {
+
+// ---------------------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(POLAR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define POLAR_CUDA(call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------------------- code tables
+__device__ DevCode g_codes[POLAR_MAX_CODES];
+
+struct DeviceCodes {
+    bool init = false;
+    DevCode* base = nullptr;  // device address of g_codes on this device
+    std::vector<DevCode> host;  // host copies of the filled slots, in slot order
+};
+static std::mutex g_codes_mutex;
+static std::vector<DeviceCodes> g_dev;
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+static int log2i(int v)
+{
+    int n = 0;
+    while ((1 << n) < v) ++n;
+    return n;
+}
+
+static int check_code(const polar_code* code)
+{
+    if (!code) return fail(POLAR_ERR_ARG, "code is NULL");
+    const int N = code->N, K = code->K, c = code->crc_len;
+    if (!is_pow2(N) || N < POLAR_MIN_N || N > POLAR_MAX_N)
+        return fail(POLAR_ERR_ARG, "N = %d: must be a power of two in [%d, %d]", N, POLAR_MIN_N, POLAR_MAX_N);
+    if (!(c == 0 || c == 8 || c == 16 || c == 24)) return fail(POLAR_ERR_ARG, "crc_len = %d: must be 0, 8, 16 or 24", c);
+    if (K < c || K > N) return fail(POLAR_ERR_ARG, "K = %d: must satisfy crc_len <= K <= N", K);
+    if (c > 0 && (code->crc_poly >> c) != 0) return fail(POLAR_ERR_ARG, "crc_poly has bits above x^%d", c - 1);
+    if (!code->frozen) return fail(POLAR_ERR_ARG, "frozen table is NULL");
+    int info = 0;
+    for (int i = 0; i < N; ++i) info += code->frozen[i] ? 0 : 1;
+    if (info != K) return fail(POLAR_ERR_ARG, "frozen table has %d information positions, K = %d", info, K);
+    return POLAR_OK;
+}
+
+// Derived tables of a code: information indices in ascending order, payload position of each
+// node, and the syndrome column x^(K-1-k) mod g(x) of each information node.
+static void derive_code(const polar_code* code, DevCode& d)
+{
+    memset(&d, 0, sizeof d);
+    d.N = code->N;
+    d.n = log2i(code->N);
+    d.K = code->K;
+    d.c = code->crc_len;
+    d.P = code->K - code->crc_len;
+    d.poly = code->crc_poly;
+    std::vector<int> info;
+    for (int i = 0; i < d.N; ++i) {
+        d.paypos[i] = -1;
+        if (code->frozen[i])
+            d.frozen_bits[i >> 5] |= 1u << (i & 31);
+        else
+            info.push_back(i);
+    }
+    // powers x^m mod g(x), m = 0..K-1, by repeated multiplication with x
+    std::vector<uint32_t> pw(d.K > 0 ? d.K : 1);
+    uint32_t r = 1;
+    const uint32_t top = d.c > 0 ? (1u << d.c) : 0u;
+    for (int m = 0; m < d.K; ++m) {
+        pw[m] = d.c > 0 ? r : 0u;
+        if (d.c > 0) {
+            r <<= 1;
+            if (r & top) r ^= top | d.poly;
+        }
+    }
+    for (int k = 0; k < d.K; ++k) {
+        const int j = info[k];
+        d.info_idx[k] = (int16_t)j;
+        d.colsyn[j] = pw[d.K - 1 - k];
+        if (k < d.P) d.paypos[j] = (int16_t)k;
+    }
+}
+
+// Device pointer of the table slot holding `code` on the current device; fills a free slot on
+// first use (an asynchronous copy on `stream`).
+static int code_slot(const polar_code* code, cudaStream_t stream, const DevCode** out)
+{
+    int rc = check_code(code);
+    if (rc) return rc;
+    DevCode d;
+    derive_code(code, d);
+    int dev = 0;
+    POLAR_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_codes_mutex);
+    if ((int)g_dev.size() <= dev) g_dev.resize(dev + 1);
+    DeviceCodes& dc = g_dev[dev];
+    if (!dc.init) {
+        dc.host.reserve(POLAR_MAX_CODES);
+        void* p = nullptr;
+        POLAR_CUDA(cudaGetSymbolAddress(&p, g_codes));
+        dc.base = static_cast<DevCode*>(p);
+        dc.init = true;
+    }
+    for (size_t s = 0; s < dc.host.size(); ++s) {
+        if (memcmp(&dc.host[s], &d, sizeof d) == 0) {
+            *out = dc.base + s;
+            return POLAR_OK;
+        }
+    }
+    if ((int)dc.host.size() >= POLAR_MAX_CODES)
+        return fail(POLAR_ERR_CAPACITY, "more than %d distinct codes used on device %d", POLAR_MAX_CODES, dev);
+    dc.host.push_back(d);
+    const size_t s = dc.host.size() - 1;
+    cudaError_t e = cudaMemcpyAsync(dc.base + s, &dc.host[s], sizeof(DevCode), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        dc.host.pop_back();
+        return cuda_fail(e, "upload of a code table");
+    }
+    *out = dc.base + s;
+    return POLAR_OK;
+}
+
+// ---------------------------------------------------------------------------- workspace
+// [header 256 B: fail count, SCL work counter, status word][fail list: int32 x B][SCL scratch]
+struct WsHeader {
+    int fail_count;
+    int scl_next;
+    int err;
+};
+constexpr size_t kHeaderBytes = 256;
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static size_t scl_scratch_bytes(int N, int L, int B)
+{
+    if (scl_fits_smem(N, L)) return 0;
+    return (size_t)scl_resident_warps(N, L) * scl_global_warp_bytes(N, L);
+    (void)B;
+}
+
+static size_t ws_bytes(const polar_code* code, int B, int L, int op)
+{
+    if (op == POLAR_OP_BP) return 0;
+    size_t b = kHeaderBytes;
+    if (op == POLAR_OP_HYBRID) b += align_up(sizeof(int) * (size_t)std::max(B, 1), 256);
+    b += scl_scratch_bytes(code->N, L, B);
+    return b;
+}
+
+static int launch_bp(const DevCode* dcode, const polar_code* code, const float* llr, int B, int max_iters,
+                     float llr_max, int precision, const float* w, int w_iters, uint8_t* bits, uint8_t* status,
+                     uint16_t* iters, float* llr_u, float* llr_x, int* fail_count, int* fail_list,
+                     cudaStream_t stream)
+{
+    BPArgs a{};
+    a.llr = llr;
+    a.B = B;
+    a.max_iters = max_iters;
+    a.llr_max = llr_max;
+    a.w = w;
+    a.w_iters = w ? w_iters : 0;
+    a.bits = bits;
+    a.status = status;
+    a.iters = iters;
+    a.llr_u = llr_u;
+    a.llr_x = llr_x;
+    a.code = dcode;
+    a.fail_count = fail_count;
+    a.fail_list = fail_list;
+    a.row_bytes = (code->K - code->crc_len + 7) / 8;
+    const int n = log2i(code->N);
+    auto go = [&](auto LOGN_C) -> int {
+        constexpr int LOGN = decltype(LOGN_C)::value;
+        using Cfg = BPConfig<LOGN>;
+        using P = typename Cfg::Plan;
+        const int fpt = precision == POLAR_FP16 ? 2 : 1;
+        const int groups = (B + fpt - 1) / fpt;
+        const int grid = (groups + Cfg::F - 1) / Cfg::F;
+        const size_t smem = (size_t)Cfg::F * bp_slot_words<P>() * 4;
+        const int threads = Cfg::F * P::T;
+        constexpr int TH = Cfg::F * P::T;
+        if (precision == POLAR_FP16) {
+            if (w) bp_kernel<LOGN, __half2, true, TH><<<grid, threads, smem, stream>>>(a);
+            else bp_kernel<LOGN, __half2, false, TH><<<grid, threads, smem, stream>>>(a);
+        } else {
+            if (w) bp_kernel<LOGN, float, true, TH><<<grid, threads, smem, stream>>>(a);
+            else bp_kernel<LOGN, float, false, TH><<<grid, threads, smem, stream>>>(a);
+        }
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? POLAR_OK : cuda_fail(e, "bp_kernel launch");
+    };
+    if (B == 0) return POLAR_OK;
+    switch (n) {
+        case 7: return go(std::integral_constant<int, 7>{});
+        case 8: return go(std::integral_constant<int, 8>{});
+        case 9: return go(std::integral_constant<int, 9>{});
+        case 10: return go(std::integral_constant<int, 10>{});
+        case 11: return go(std::integral_constant<int, 11>{});
+        default: return fail(POLAR_ERR_ARG, "unsupported N = %d", code->N);
+    }
+}
+
+static int check_bp_args(const polar_code* code, const float* llr, int B, int max_iters, float llr_max,
+                         int precision, const float* w, int w_iters, const uint8_t* bits, const uint8_t* status,
+                         const uint16_t* iters)
+{
+    const int rc = check_code(code);
+    if (rc) return rc;
+    if (B < 0) return fail(POLAR_ERR_ARG, "B = %d < 0", B);
+    if (max_iters < 1 || max_iters > 65535) return fail(POLAR_ERR_ARG, "max_iters = %d: must be in [1, 65535]", max_iters);
+    if (!(llr_max > 0.0f) || !std::isfinite(llr_max)) return fail(POLAR_ERR_ARG, "llr_max must be finite and > 0");
+    if (precision != POLAR_FP32 && precision != POLAR_FP16) return fail(POLAR_ERR_ARG, "precision = %d", precision);
+    if (precision == POLAR_FP16 && llr_max > 32768.0f) return fail(POLAR_ERR_ARG, "llr_max > 32768 with FP16 messages");
+    if (w && w_iters < 1) return fail(POLAR_ERR_ARG, "wms_iters = %d with weights given", w_iters);
+    if (B > 0 && (!llr || !status || !iters)) return fail(POLAR_ERR_ARG, "NULL llr/status/iters");
+    if (B > 0 && !bits && code->K > code->crc_len) return fail(POLAR_ERR_ARG, "NULL bits");
+    return POLAR_OK;
+}
+
+static const int kListSizes[] = {1, 2, 4, 8, 16, 32};
+static bool valid_L(int L)
+{
+    for (int v : kListSizes)
+        if (v == L) return true;
+    return false;
+}
+
+static int launch_scl(const DevCode* dcode, const polar_code* code, const float* llr, int B, int L,
+                      uint8_t* bits, uint8_t* status, const int* list, const int* count, int* next,
+                      void* scratch, cudaStream_t stream)
+{
+    SCLArgs a{};
+    a.llr = llr;
+    a.B = B;
+    a.L = L;
+    a.bits = bits;
+    a.status = status;
+    a.code = dcode;
+    a.list = list;
+    a.count = count;
+    a.next = next;
+    a.scratch = static_cast<float*>(scratch);
+    a.row_bytes = (code->K - code->crc_len + 7) / 8;
+    const cudaError_t e = scl_launch(a, code->N, L, stream);
+    return e == cudaSuccess ? POLAR_OK : cuda_fail(e, "scl_kernel launch");
+}
+
+}  // namespace polar
+
+using namespace polar;
+
+// ==================================================================================== C ABI
+extern "C" {
+
+const char* polar_last_error(void) { return g_last_error.c_str(); }
+
+int polar_construct(int32_t N, int32_t K, double design_ebn0_db, double design_rate, uint8_t* frozen_out,
+                    int32_t* info_idx_out)
+{
+    if (!is_pow2(N) || N < 2 || N > (1 << 20)) return fail(POLAR_ERR_ARG, "N = %d: power of two in [2, 2^20]", N);
+    if (K < 0 || K > N) return fail(POLAR_ERR_ARG, "K = %d outside [0, N]", K);
+    if (!(design_rate > 0.0) || !std::isfinite(design_ebn0_db)) return fail(POLAR_ERR_ARG, "bad design point");
+    if (!frozen_out) return fail(POLAR_ERR_ARG, "frozen_out is NULL");
+    const int n = log2i(N);
+    // ln Z of every bit-channel, one combining level at a time: each level splits every channel
+    // into its minus (index bit 0) and plus (index bit 1) child, so the first level decides the
+    // index MSB.  minus: ln(2Z - Z^2), plus: 2 ln Z.
+    std::vector<double> lz(1, -design_rate * std::pow(10.0, design_ebn0_db / 10.0)), next;
+    for (int level = 0; level < n; ++level) {
+        next.resize(lz.size() * 2);
+        for (size_t i = 0; i < lz.size(); ++i) {
+            const double v = lz[i];
+            double minus;
+            if (v <= -M_LN2) {
+                minus = v + std::log(2.0 - std::exp(v));
+            } else {
+                const double d = -std::expm1(v);  // 1 - Z, accurate near Z = 1
+                minus = std::log1p(-(d * d));
+            }
+            next[2 * i] = minus;
+            next[2 * i + 1] = 2.0 * v;
+        }
+        lz.swap(next);
+    }
+    std::vector<int> order(N);
+    for (int i = 0; i < N; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (lz[a] != lz[b]) return lz[a] < lz[b];
+        return a > b;  // equal reliability: the larger index counts as more reliable
+    });
+    for (int i = 0; i < N; ++i) frozen_out[i] = 1;
+    for (int k = 0; k < K; ++k) frozen_out[order[k]] = 0;
+    if (info_idx_out) {
+        int k = 0;
+        for (int i = 0; i < N; ++i)
+            if (!frozen_out[i]) info_idx_out[k++] = i;
+    }
+    return POLAR_OK;
+}
+
+int polar_encode(const polar_code* code, const uint8_t* payload, int32_t B, uint8_t* codeword, void* stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (B < 0) return fail(POLAR_ERR_ARG, "B < 0");
+    const DevCode* d = nullptr;
+    int rc = code_slot(code, st, &d);
+    if (rc) return rc;
+    if (B == 0) return POLAR_OK;
+    if (!payload || !codeword) return fail(POLAR_ERR_ARG, "NULL payload/codeword");
+    const int warps = 4;
+    encode_kernel<<<(B + warps - 1) / warps, warps * 32, 0, st>>>(d, payload, B, (code->K - code->crc_len + 7) / 8,
+                                                                codeword);
+    POLAR_CUDA(cudaGetLastError());
+    return POLAR_OK;
+}
+
+int polar_random_payload(int32_t B, int32_t P, uint64_t seed, uint64_t frame0, uint8_t* payload, void* stream)
+{
+    if (B < 0 || P < 0) return fail(POLAR_ERR_ARG, "B or P < 0");
+    if (B == 0 || P == 0) return POLAR_OK;
+    if (!payload) return fail(POLAR_ERR_ARG, "NULL payload");
+    const long long total = (long long)B * (((P + 31) / 32 + 3) / 4);
+    random_payload_kernel<<<(unsigned)((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        B, P, seed, frame0, payload);
+    POLAR_CUDA(cudaGetLastError());
+    return POLAR_OK;
+}
+
+int polar_awgn_llr(const uint8_t* codeword, int32_t B, int32_t N, float sigma, uint64_t seed, uint64_t frame0,
+                   float* llr, void* stream)
+{
+    if (B < 0 || !is_pow2(N) || N < 8 || !(sigma > 0.0f)) return fail(POLAR_ERR_ARG, "bad B, N or sigma");
+    if (B == 0) return POLAR_OK;
+    if (!codeword || !llr) return fail(POLAR_ERR_ARG, "NULL codeword/llr");
+    const long long total = (long long)B * (N / 4);
+    awgn_llr_kernel<<<(unsigned)((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        codeword, B, N, sigma, seed, frame0, llr);
+    POLAR_CUDA(cudaGetLastError());
+    return POLAR_OK;
+}
+
+size_t polar_workspace_bytes(const polar_code* code, int32_t B, int32_t L, int32_t op)
+{
+    if (check_code(code) != POLAR_OK || B < 0) return 0;
+    if (op != POLAR_OP_BP && !valid_L(L)) return 0;
+    if (op < POLAR_OP_BP || op > POLAR_OP_HYBRID) return 0;
+    return ws_bytes(code, B, L, op);
+}
+
+int bp_decode(const polar_code* code, const float* llr, int32_t B, int32_t max_iters, float llr_max,
+              int32_t precision, const float* wms_scales, int32_t wms_iters, uint8_t* bits, uint8_t* status,
+              uint16_t* iters, float* llr_u, float* llr_x, void* workspace, size_t ws, void* stream)
+{
+    (void)workspace;
+    (void)ws;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_bp_args(code, llr, B, max_iters, llr_max, precision, wms_scales, wms_iters, bits, status, iters);
+    if (rc) return rc;
+    const DevCode* d = nullptr;
+    if ((rc = code_slot(code, st, &d))) return rc;
+    return launch_bp(d, code, llr, B, max_iters, llr_max, precision, wms_scales, wms_iters, bits, status, iters,
+                     llr_u, llr_x, nullptr, nullptr, st);
+}
+
+int scl_decode(const polar_code* code, const float* llr, int32_t B, int32_t L, uint8_t* bits, uint8_t* status,
+               void* workspace, size_t ws, void* stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_code(code);
+    if (rc) return rc;
+    if (B < 0) return fail(POLAR_ERR_ARG, "B < 0");
+    if (!valid_L(L)) return fail(POLAR_ERR_ARG, "L = %d: must be 1, 2, 4, 8, 16 or 32", L);
+    const DevCode* d = nullptr;
+    rc = code_slot(code, st, &d);
+    if (rc) return rc;
+    if (B == 0) return POLAR_OK;
+    if (!llr || !status || (!bits && code->K > code->crc_len)) return fail(POLAR_ERR_ARG, "NULL llr/bits/status");
+    const size_t need = ws_bytes(code, B, L, POLAR_OP_SCL);
+    if (!workspace || ws < need) return fail(POLAR_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws, need);
+    char* base = static_cast<char*>(workspace);
+    WsHeader* h = reinterpret_cast<WsHeader*>(base);
+    POLAR_CUDA(cudaMemsetAsync(h, 0, sizeof(WsHeader), st));
+    return launch_scl(d, code, llr, B, L, bits, status, nullptr, nullptr, &h->scl_next, base + kHeaderBytes, st);
+}
+
+int hybrid_decode(const polar_code* code, const float* llr, int32_t B, int32_t max_iters, float llr_max,
+                  int32_t precision, const float* wms_scales, int32_t wms_iters, int32_t L, uint8_t* bits,
+                  uint8_t* status, uint16_t* iters, void* workspace, size_t ws, void* stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_bp_args(code, llr, B, max_iters, llr_max, precision, wms_scales, wms_iters, bits, status, iters);
+    if (rc) return rc;
+    if (!valid_L(L)) return fail(POLAR_ERR_ARG, "L = %d: must be 1, 2, 4, 8, 16 or 32", L);
+    const DevCode* d = nullptr;
+    if ((rc = code_slot(code, st, &d))) return rc;
+    if (B == 0) return POLAR_OK;
+    const size_t need = ws_bytes(code, B, L, POLAR_OP_HYBRID);
+    if (!workspace || ws < need) return fail(POLAR_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws, need);
+    char* base = static_cast<char*>(workspace);
+    WsHeader* h = reinterpret_cast<WsHeader*>(base);
+    int* list = reinterpret_cast<int*>(base + kHeaderBytes);
+    void* scratch = base + kHeaderBytes + align_up(sizeof(int) * (size_t)B, 256);
+    POLAR_CUDA(cudaMemsetAsync(h, 0, sizeof(WsHeader), st));
+    if ((rc = launch_bp(d, code, llr, B, max_iters, llr_max, precision, wms_scales, wms_iters, bits, status, iters,
+                        nullptr, nullptr, &h->fail_count, list, st)))
+        return rc;
+    return launch_scl(d, code, llr, B, L, bits, status, list, &h->fail_count, &h->scl_next, scratch, st);
+}
+
+int polar_hybrid_fallback_count(const void* workspace, int32_t* out, void* stream)
+{
+    if (!workspace || !out) return fail(POLAR_ERR_ARG, "NULL workspace/out");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int v = 0;
+    POLAR_CUDA(cudaMemcpyAsync(&v, workspace, sizeof(int), cudaMemcpyDeviceToHost, st));
+    POLAR_CUDA(cudaStreamSynchronize(st));
+    *out = v;
+    return POLAR_OK;
+}
+
+}  // extern "C"

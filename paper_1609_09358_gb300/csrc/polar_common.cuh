@@ -1,0 +1,81 @@
+// polar_common.cuh -- shared device-side definitions of the GB300 polar decoder.
+#pragma once
+
+#include <cstdint>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "polar_gb300.h"
+
+namespace polar {
+
+constexpr int kMaxN = POLAR_MAX_N;
+constexpr int kMaxWords = kMaxN / 32;
+
+// Per-code tables derived on the host from (N, K, frozen, CRC) and kept in a static device
+// array, one slot per distinct code.
+struct DevCode {
+    int32_t N, n, K, P, c;
+    uint32_t poly;
+    uint32_t frozen_bits[kMaxWords];  // bit i of word i/32 set = node i frozen
+    // Syndrome column of node i: x^(K-1-k) mod g(x) for the node's information index k, 0 for a
+    // frozen node.  The XOR of the columns of the information nodes decided 1 is the remainder of
+    // the decided K-bit word divided by g(x): zero iff the CRC holds.
+    uint32_t colsyn[kMaxN];
+    int16_t paypos[kMaxN];    // payload position of node i, -1 for frozen and CRC nodes
+    int16_t info_idx[kMaxN];  // node of information index k (k < K)
+};
+
+// ---------------------------------------------------------------------------- FP32 primitives
+// min-sum PE function g(a, b) = sign(a) sign(b) min(|a|, |b|) as one instruction: the magnitude
+// is min(|a|, |b|), the sign bit the XOR of the operands' sign bits.
+__device__ __forceinline__ float xmin(float a, float b)
+{
+    float d;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+// Clip to [-m, m] for m > 0, also as one instruction: sign(x) xor sign(m) = sign(x).
+__device__ __forceinline__ float clipm(float x, float m) { return xmin(x, m); }
+
+// Staging clip of a channel LLR: NaN reads as 0 (an erasure), then [-m, m].
+__device__ __forceinline__ float stage_clip(float v, float m)
+{
+    v = (v == v) ? v : 0.0f;
+    return fminf(fmaxf(v, -m), m);
+}
+
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+
+// ---------------------------------------------------------------------------- half2 primitives
+__device__ __forceinline__ __half2 xmin(__half2 a, __half2 b)
+{
+    uint32_t d;
+    asm("min.xorsign.abs.f16x2 %0, %1, %2;"
+        : "=r"(d)
+        : "r"(*reinterpret_cast<uint32_t*>(&a)), "r"(*reinterpret_cast<uint32_t*>(&b)));
+    return *reinterpret_cast<__half2*>(&d);
+}
+__device__ __forceinline__ __half2 clipm(__half2 x, __half2 m) { return xmin(x, m); }
+__device__ __forceinline__ __half2 fadd(__half2 a, __half2 b) { return __hadd2(a, b); }
+__device__ __forceinline__ __half2 fmul(__half2 a, __half2 b) { return __hmul2(a, b); }
+
+// ---------------------------------------------------------------------------- barriers
+// Synchronise the T threads that decode one frame: the warp itself for T <= 32, otherwise the
+// whole CTA (plans with T > 32 put one frame group in a CTA).
+template <int T>
+__device__ __forceinline__ void frame_sync(int slot)
+{
+    (void)slot;
+    if constexpr (T <= 32) {
+        __syncwarp();
+    } else {
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ int frozen_at(const uint32_t* fb, int i) { return (fb[i >> 5] >> (i & 31)) & 1; }
+
+}  // namespace polar

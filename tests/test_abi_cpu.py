@@ -1,0 +1,71 @@
+"""The C-ABI library: builds, loads and exports every symbol of include/polar_gb300.h; host-only
+entry points (construction, argument checks) behave as documented.  No GPU needed."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1609_09358_gb300 import api, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "polar_gb300.h")
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:int|size_t|char\s*\*|void)\s*\*?\s*(\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return api.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = header_functions()
+    assert len(names) >= 10, names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(api.SIGNATURES), set(names) ^ set(api.SIGNATURES)
+
+
+@pytest.mark.parametrize("N,K,design_db", [(8, 4, 0.0), (128, 64, 0.0), (256, 100, 1.0), (1024, 512, 0.0),
+                                           (2048, 1024, 0.0), (2048, 1024, -2.0), (512, 384, 3.0), (64, 1, 0.0),
+                                           (64, 64, 0.0), (4096, 2048, 0.0)])
+def test_construct_matches_oracle(lib, N, K, design_db):
+    rate = 0.5
+    f_lib, info_lib = api.polar_construct(N, K, design_db, rate)
+    f_or, info_or, _ = oracle.construct(N, K, design_db, rate)
+    assert np.array_equal(f_lib, f_or)
+    assert np.array_equal(info_lib, info_or)
+
+
+def test_argument_errors_without_gpu(lib):
+    assert lib.polar_construct(100, 10, 0.0, 0.5, None, None) == -1
+    assert "power of two" in lib.polar_last_error().decode()
+    frozen = np.ones(100, np.uint8)
+    bad = api.PolarCode(100, 0, 0, frozen)
+    rc = lib.bp_decode(bad.ref(), None, 4, 10, 20.0, 0, None, 0, None, None, None, None, None, None, 0, None)
+    assert rc == -1 and "N = 100" in lib.polar_last_error().decode()
+    good = api.PolarCode(128, 64, 8, oracle.make_code(128, 64, 8).frozen)
+    rc = lib.bp_decode(good.ref(), None, 4, 0, 20.0, 0, None, 0, None, None, None, None, None, None, 0, None)
+    assert rc == -1 and "max_iters" in lib.polar_last_error().decode()
+    rc = lib.hybrid_decode(good.ref(), None, 4, 10, 20.0, 0, None, 0, 3, None, None, None, None, 0, None)
+    assert rc == -1
+    wrongk = api.PolarCode(128, 63, 8, good.frozen)
+    rc = lib.scl_decode(wrongk.ref(), None, 4, 8, None, None, None, 0, None)
+    assert rc == -1 and "information positions" in lib.polar_last_error().decode()
+    assert lib.polar_workspace_bytes(bad.ref(), 10, 8, 2) == 0
+    assert lib.polar_workspace_bytes(good.ref(), 10, 8, 0) == 0
+    assert lib.polar_workspace_bytes(good.ref(), 10, 3, 1) == 0
+
+
+def test_bit_packing_roundtrip():
+    rng = np.random.default_rng(0)
+    b = rng.integers(0, 2, (5, 61), dtype=np.uint8)
+    assert np.array_equal(api.unpack_bits(api.pack_bits(b), 61), b)

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA decoder through the C ABI against the CPU oracle, element by element.
+
+FP32 BP, SCL and hybrid are compared bit-exactly (decided bits, per-frame status and iteration
+counts, and the output LLRs as float32 values); the half-precision BP bit-exactly against the
+oracle's binary16 emulation.  Inputs are seeded frames built on the CPU (tests/frames.py).  Batch
+sizes are chosen so that the CTA grid has a ragged tail (B not a multiple of the frames per CTA).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests import frames as fr
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+from paper_1609_09358_gb300 import api, build  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    api.load()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_bp(ocode, llr, max_iters, llr_max, precision=api.POLAR_FP32, w=None, want_llr=True):
+    code = fr.api_code(ocode)
+    B, N = llr.shape
+    bits = torch.zeros((B, code.row_bytes), dtype=torch.uint8, device="cuda")
+    status = torch.zeros(B, dtype=torch.uint8, device="cuda")
+    iters = torch.zeros(B, dtype=torch.int16, device="cuda")
+    lu = torch.zeros((B, N), dtype=torch.float32, device="cuda") if want_llr else None
+    lx = torch.zeros((B, N), dtype=torch.float32, device="cuda") if want_llr else None
+    api.bp_decode(code, dev(llr), max_iters, llr_max, precision, None if w is None else dev(w), bits, status, iters,
+                  lu, lx)
+    torch.cuda.synchronize()
+    out = {"bits": api.unpack_bits(bits.cpu().numpy(), ocode.P), "status": status.cpu().numpy(),
+           "iters": iters.cpu().numpy().astype(np.int32)}
+    if want_llr:
+        out["llr_u"] = lu.cpu().numpy()
+        out["llr_x"] = lx.cpu().numpy()
+    return out
+
+
+def assert_bp_equal(got, ref, ocode, with_llr=True):
+    assert np.array_equal(got["iters"], ref["iters"]), np.nonzero(got["iters"] != ref["iters"])[0][:10]
+    assert np.array_equal(got["status"], ref["status"])
+    assert np.array_equal(got["bits"], oracle.payload_of(ref["u_hat"], ocode))
+    if with_llr:
+        assert np.array_equal(got["llr_u"], ref["llr_u"]), np.max(np.abs(got["llr_u"] - ref["llr_u"]))
+        assert np.array_equal(got["llr_x"], ref["llr_x"]), np.max(np.abs(got["llr_x"] - ref["llr_x"]))
+
+
+BP_CASES = [
+    # N, K, crc, Eb/N0, B, max_iters
+    (128, 64, 8, 2.5, 203, 50),
+    (128, 64, 8, 0.5, 61, 50),
+    (256, 128, 16, 2.0, 97, 60),
+    (512, 256, 16, 2.0, 45, 60),
+    (1024, 512, 16, 2.5, 37, 200),
+    (1024, 512, 16, 1.0, 12, 200),
+    (2048, 1024, 24, 1.5, 9, 80),
+    (1024, 768, 16, 3.0, 21, 100),
+    (256, 64, 16, 1.0, 33, 40),
+]
+
+
+@pytest.mark.parametrize("N,K,crc,ebn0,B,imax", BP_CASES)
+def test_bp_fp32_bit_exact(N, K, crc, ebn0, B, imax):
+    ocode = fr.oracle_code(N, K, crc)
+    _, llr = fr.frames(ocode, ebn0, B, seed=1000 + N + K)
+    ref = oracle.bp_decode(llr, ocode, imax, 20.0, "f32")
+    got = run_bp(ocode, llr, imax, 20.0)
+    assert_bp_equal(got, ref, ocode)
+
+
+@pytest.mark.parametrize("N,K,crc,ebn0,B,imax", [c for c in BP_CASES if c[0] <= 1024][:6] + [(2048, 1024, 24, 1.5, 9, 80)])
+def test_bp_fp16_bit_exact_vs_binary16_emulation(N, K, crc, ebn0, B, imax):
+    ocode = fr.oracle_code(N, K, crc)
+    _, llr = fr.frames(ocode, ebn0, B, seed=2000 + N + K)
+    ref = oracle.bp_decode(llr, ocode, imax, 32.0, "f16")
+    got = run_bp(ocode, llr, imax, 32.0, api.POLAR_FP16)
+    assert_bp_equal(got, ref, ocode)
+
+
+@pytest.mark.parametrize("N,K,crc", [(128, 64, 8), (1024, 512, 16), (512, 256, 16)])
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_bp_weighted_bit_exact(N, K, crc, precision):
+    ocode = fr.oracle_code(N, K, crc)
+    _, llr = fr.frames(ocode, 1.5, 19, seed=3000 + N)
+    rng = np.random.default_rng(N)
+    T = 6
+    w = rng.uniform(0.5, 1.5, (T, 2, ocode.n, N)).astype(np.float32)
+    M = 20.0 if precision == "f32" else 32.0
+    ref = oracle.bp_decode(llr, ocode, 10, M, precision, w=w)
+    got = run_bp(ocode, llr, 10, M, api.POLAR_FP32 if precision == "f32" else api.POLAR_FP16, w=w)
+    assert_bp_equal(got, ref, ocode)
+
+
+def test_bp_edge_inputs():
+    """NaN reads as an erasure, +-inf clips, max_iters = 1, a single frame."""
+    ocode = fr.oracle_code(256, 128, 16)
+    _, llr = fr.frames(ocode, 2.0, 5, seed=5)
+    llr[0, :7] = np.nan
+    llr[1, ::3] = np.inf
+    llr[2, ::5] = -np.inf
+    llr[3] = 0.0
+    for imax in (1, 25):
+        ref = oracle.bp_decode(llr, ocode, imax, 20.0, "f32")
+        got = run_bp(ocode, llr, imax, 20.0)
+        assert_bp_equal(got, ref, ocode)
+    ref = oracle.bp_decode(llr[:1], ocode, 25, 20.0, "f32")
+    assert_bp_equal(run_bp(ocode, llr[:1], 25, 20.0), ref, ocode)
+
+
+def test_bp_degenerate_codes():
+    """No CRC (the check is void, BP stops after one iteration), K = N (nothing frozen), P = 0."""
+    for N, K, crc in [(128, 64, 0), (128, 128, 16), (256, 16, 16)]:
+        frozen, info, _ = oracle.construct(N, K, 0.0, 0.5)
+        ocode = oracle.Code(N, K, crc, oracle.CRC_POLYS[crc], frozen, info)
+        rng = np.random.default_rng(N + K)
+        llr = rng.normal(1.0, 2.0, (13, N)).astype(np.float32)
+        ref = oracle.bp_decode(llr, ocode, 20, 20.0, "f32")
+        got = run_bp(ocode, llr, 20, 20.0)
+        assert_bp_equal(got, ref, ocode)
+
+
+def run_scl(ocode, llr, L):
+    code = fr.api_code(ocode)
+    B = llr.shape[0]
+    bits = torch.zeros((B, code.row_bytes), dtype=torch.uint8, device="cuda")
+    status = torch.zeros(B, dtype=torch.uint8, device="cuda")
+    ws = torch.zeros(max(api.polar_workspace_bytes(code, B, L, api.POLAR_OP_SCL), 256), dtype=torch.uint8,
+                     device="cuda")
+    api.scl_decode(code, dev(llr), L, bits, status, ws)
+    torch.cuda.synchronize()
+    return api.unpack_bits(bits.cpu().numpy(), ocode.P), status.cpu().numpy()
+
+
+SCL_CASES = [
+    # N, K, crc, Eb/N0, B, L
+    (128, 64, 8, 1.0, 50, 4),
+    (128, 64, 8, 1.0, 30, 1),
+    (128, 64, 8, 0.0, 30, 32),
+    (256, 128, 16, 1.0, 24, 8),
+    (256, 128, 16, 1.0, 12, 2),
+    (512, 256, 16, 1.0, 10, 16),
+    (1024, 512, 16, 1.0, 12, 8),
+    (2048, 1024, 24, 1.0, 4, 8),
+]
+
+
+@pytest.mark.parametrize("N,K,crc,ebn0,B,L", SCL_CASES)
+def test_scl_bit_exact(N, K, crc, ebn0, B, L):
+    ocode = fr.oracle_code(N, K, crc)
+    _, llr = fr.frames(ocode, ebn0, B, seed=4000 + N + L)
+    ref = oracle.scl_decode(llr, ocode, L, "f32")
+    bits, status = run_scl(ocode, llr, L)
+    assert np.array_equal(status, ref["status"])
+    assert np.array_equal(bits, oracle.payload_of(ref["u_hat"], ocode))
+
+
+def test_scl_global_scratch_path():
+    """L = 32 at N = 2048 keeps the list's LLR arrays in the device workspace."""
+    ocode = fr.oracle_code(2048, 1024, 24)
+    _, llr = fr.frames(ocode, 1.0, 3, seed=77)
+    ref = oracle.scl_decode(llr, ocode, 32, "f32")
+    bits, status = run_scl(ocode, llr, 32)
+    assert np.array_equal(status, ref["status"])
+    assert np.array_equal(bits, oracle.payload_of(ref["u_hat"], ocode))
+
+
+def run_hybrid(ocode, llr, imax, L, llr_max=20.0, precision=api.POLAR_FP32):
+    code = fr.api_code(ocode)
+    B = llr.shape[0]
+    dec = api.Decoder(code, B, L)
+    dec.hybrid(dev(llr), imax, llr_max, precision)
+    torch.cuda.synchronize()
+    nfb = api.polar_hybrid_fallback_count(dec.workspace)
+    return (api.unpack_bits(dec.bits.cpu().numpy(), ocode.P), dec.status.cpu().numpy(),
+            dec.iters.cpu().numpy().astype(np.int32), nfb)
+
+
+@pytest.mark.parametrize("N,K,crc,ebn0,B,imax,L", [
+    (128, 64, 8, 2.5, 1000, 50, 4),   # the small plain-hybrid workload in full
+    (128, 64, 8, 1.0, 300, 50, 4),
+    (1024, 512, 16, 2.0, 160, 200, 8),
+    (1024, 512, 16, 1.0, 24, 30, 8),
+    (512, 256, 16, 1.5, 70, 40, 16),
+])
+def test_hybrid_bit_exact(N, K, crc, ebn0, B, imax, L):
+    ocode = fr.oracle_code(N, K, crc)
+    _, llr = fr.frames(ocode, ebn0, B, seed=5000 + N)
+    ref = oracle.hybrid_decode(llr, ocode, imax, 20.0, L, precision="f32")
+    bits, status, iters, nfb = run_hybrid(ocode, llr, imax, L)
+    assert np.array_equal(iters, ref["iters"])
+    assert np.array_equal(status, ref["status"])
+    assert np.array_equal(bits, oracle.payload_of(ref["u_hat"], ocode))
+    assert nfb == int(np.sum(ref["status"] != oracle.BP_OK))
+
+
+def test_hybrid_full_size_sampled():
+    """The production workload as the benchmark launches it (N = 1024, K = 512, CRC-16, 1e5 frames,
+    i_max = 200, L = 8, 2.5 dB): every frame's status and the decoded bits of a random sample plus
+    every SCL frame are compared with the oracle, which decodes those frames one by one."""
+    ocode = fr.oracle_code(1024, 512, 16)
+    B = 100_000
+    pay, llr = fr.frames_large(ocode, 2.5, B, seed=1609093582)
+    bits, status, iters, nfb = run_hybrid(ocode, llr, 200, 8)
+    rng = np.random.default_rng(0)
+    fb = np.nonzero(status != oracle.BP_OK)[0]
+    sample = np.unique(np.concatenate([rng.choice(B, 200, replace=False), fb[:200]]))
+    ref = oracle.hybrid_decode(llr[sample], ocode, 200, 20.0, 8, precision="f32")
+    assert np.array_equal(iters[sample], ref["iters"])
+    assert np.array_equal(status[sample], ref["status"])
+    assert np.array_equal(bits[sample], oracle.payload_of(ref["u_hat"], ocode))
+    assert nfb == len(fb)
+    # properties that hold at any size: BP_OK frames pass the CRC, statuses are valid
+    assert set(np.unique(status)) <= {1, 2, 3}
+    ok = status == oracle.BP_OK
+    assert np.all(iters[ok] >= 1) and np.all(iters[~ok] == 200)
+
+
+def test_encoder_bit_exact():
+    for N, K, crc in [(128, 64, 8), (256, 100, 16), (1024, 512, 16), (2048, 1024, 24), (512, 24, 24)]:
+        ocode = fr.oracle_code(N, K, crc)
+        code = fr.api_code(ocode)
+        from paper_1609_09358_gb300 import inputs
+        pay = inputs.payload_bits(9, 0, 67, ocode.P)
+        x_ref = oracle.encode_batch(pay, ocode)
+        cw = torch.zeros((67, N // 8), dtype=torch.uint8, device="cuda")
+        api.polar_encode(code, dev(api.pack_bits(pay)), cw)
+        torch.cuda.synchronize()
+        assert np.array_equal(api.unpack_bits(cw.cpu().numpy(), N), x_ref)
+
+
+def test_generators_match_cpu_stream():
+    from paper_1609_09358_gb300 import inputs
+    B, P, N = 37, 496, 1024
+    pay = torch.zeros((B, (P + 7) // 8), dtype=torch.uint8, device="cuda")
+    api.polar_random_payload(B, P, 1234, 77, pay)
+    torch.cuda.synchronize()
+    assert np.array_equal(api.unpack_bits(pay.cpu().numpy(), P), inputs.payload_bits(1234, 77, B, P))
+    x = np.random.default_rng(1).integers(0, 2, (B, N), dtype=np.uint8)
+    llr = torch.zeros((B, N), dtype=torch.float32, device="cuda")
+    sigma = 0.8
+    api.polar_awgn_llr(dev(api.pack_bits(x)), N, sigma, 99, 5, llr)
+    torch.cuda.synchronize()
+    z = inputs.unit_noise(99, 5, B, N)
+    ref = 2.0 * ((1.0 - 2.0 * x) + sigma * z) / sigma ** 2
+    assert np.allclose(llr.cpu().numpy(), ref, rtol=1e-4, atol=1e-4)
