@@ -53,6 +53,7 @@ extern "C" {
 #define POLAR_OP_BP 0
 #define POLAR_OP_SCL 1
 #define POLAR_OP_HYBRID 2
+#define POLAR_OP_HYBRID_HOST 3
 
 #define POLAR_MIN_N 128
 #define POLAR_MAX_N 2048
@@ -143,6 +144,29 @@ int hybrid_decode(const polar_code* code, const float* llr, int32_t B, int32_t m
                   float llr_max, int32_t precision, const float* wms_scales, int32_t wms_iters,
                   int32_t L, uint8_t* bits, uint8_t* status, uint16_t* iters, void* workspace,
                   size_t ws_bytes, void* stream);
+
+/* hybrid_decode on frames that live in host memory (not a step of the paper; its Sec. III
+ * rejects moving SCL to the CPU because of transfer latency, which is what this hides).  The
+ * batch is cut into chunks of up to POLAR_HOST_CHUNK frames; each chunk's LLRs are copied to the
+ * device, decoded as in hybrid_decode and its results copied back, chunks alternating between
+ * `stream` and a second library-owned stream so that copies of one chunk overlap the decoding of
+ * the other.  The call is ordered after earlier work on `stream` and later work on `stream` is
+ * ordered after it; it returns before completion when the host buffers are page-locked.
+ *   llr_host: host float [B][N]; bits_host [B][ceil(P/8)], status_host [B], iters_host [B]:
+ *   host.  wms_scales: device or NULL.  workspace: device, >= polar_workspace_bytes(code, B, L,
+ *   POLAR_OP_HYBRID_HOST). */
+#define POLAR_HOST_CHUNK 32768
+int hybrid_decode_host(const polar_code* code, const float* llr_host, int32_t B, int32_t max_iters,
+                       float llr_max, int32_t precision, const float* wms_scales, int32_t wms_iters,
+                       int32_t L, uint8_t* bits_host, uint8_t* status_host, uint16_t* iters_host,
+                       void* workspace, size_t ws_bytes, void* stream);
+
+/* Kernel timing for measurement (not a step of the paper).  While enabled on the calling host
+ * thread, every decoder call brackets its BP and SCL kernel launches with CUDA events on the
+ * launch stream.  polar_profile_read waits for the recorded events, returns the summed device
+ * time in milliseconds and the launch count of each kernel kind, and clears the record. */
+int polar_profile_enable(int32_t on);
+int polar_profile_read(double* bp_ms, int32_t* bp_launches, double* scl_ms, int32_t* scl_launches);
 
 /* Device workspace needed by an operation (op = POLAR_OP_*) on B frames with list size L
  * (ignored for POLAR_OP_BP).  Returns 0 on invalid arguments as well as when none is needed. */

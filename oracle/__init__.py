@@ -252,7 +252,7 @@ def bp_decode(llr, code: Code, max_iters: int, llr_max: float, precision: str = 
     if w is not None:
         w = _f32(w)
         w_iters = w.shape[0]
-        assert w.shape == (w_iters, 2, code.n, N) and max_iters <= w_iters
+        assert w.shape == (w_iters, 2, code.n, N)  # iterations past w_iters run unweighted
     getattr(lib(), "or_bp_decode_batch_" + precision)(
         _p(llr, _f32p), B, N, _p(code.frozen, _u8p), _p(code.info_idx, _i32p), code.K,
         code.crc_poly, code.crc_len, max_iters, llr_max, int(early_stop), _p(w, _f32p), w_iters,

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpolar_gb300.so")
 
 POLAR_OK = 0
 POLAR_FP32, POLAR_FP16 = 0, 1
-POLAR_OP_BP, POLAR_OP_SCL, POLAR_OP_HYBRID = 0, 1, 2
+POLAR_OP_BP, POLAR_OP_SCL, POLAR_OP_HYBRID, POLAR_OP_HYBRID_HOST = 0, 1, 2, 3
 FRAME_BP_OK, FRAME_SCL_OK, FRAME_SCL_CRC_FAIL, FRAME_BP_FAIL = 1, 2, 3, 4
 CRC_POLYS = {0: 0x0, 8: 0x07, 16: 0x1021, 24: 0x864CFB}
 
@@ -48,6 +48,11 @@ SIGNATURES = {
     "scl_decode": (ctypes.c_int, [_CP, _vp, _i32, _i32, _vp, _vp, _vp, _sz, _vp]),
     "hybrid_decode": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _i32, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _sz,
                                      _vp]),
+    "hybrid_decode_host": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _i32, _vp, _i32, _i32, _vp, _vp, _vp, _vp,
+                                          _sz, _vp]),
+    "polar_profile_enable": (ctypes.c_int, [_i32]),
+    "polar_profile_read": (ctypes.c_int, [ctypes.POINTER(_f64), ctypes.POINTER(_i32), ctypes.POINTER(_f64),
+                                          ctypes.POINTER(_i32)]),
     "polar_workspace_bytes": (_sz, [_CP, _i32, _i32, _i32]),
     "polar_hybrid_fallback_count": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), _vp]),
     "polar_last_error": (ctypes.c_char_p, []),
@@ -188,6 +193,33 @@ def hybrid_decode(code: PolarCode, llr, max_iters: int, llr_max: float, precisio
     _check(load().hybrid_decode(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, _ptr(wms_scales), w_iters,
                                 L, _ptr(bits), _ptr(status), _ptr(iters), _ptr(workspace), ws_b, _stream(stream)),
            "hybrid_decode")
+
+
+def hybrid_decode_host(code: PolarCode, llr_host, max_iters: int, llr_max: float, precision: int, wms_scales, L: int,
+                       bits_host, status_host, iters_host, workspace, stream=None) -> None:
+    """Host-buffer hybrid decode: llr_host and the outputs are CPU tensors (pin them to overlap)."""
+    B = llr_host.shape[0]
+    for t in (llr_host, bits_host, status_host, iters_host):
+        if t.is_cuda or not t.is_contiguous():
+            raise PolarError("hybrid_decode_host expects contiguous host tensors")
+    w_iters = 0 if wms_scales is None else int(wms_scales.shape[0])
+    ws_b = workspace.numel() * workspace.element_size()
+    _check(load().hybrid_decode_host(code.ref(), llr_host.data_ptr(), B, max_iters, llr_max, precision,
+                                     _ptr(wms_scales), w_iters, L, bits_host.data_ptr(), status_host.data_ptr(),
+                                     iters_host.data_ptr(), _ptr(workspace), ws_b, _stream(stream)),
+           "hybrid_decode_host")
+
+
+def polar_profile_enable(on: bool) -> None:
+    _check(load().polar_profile_enable(1 if on else 0), "polar_profile_enable")
+
+
+def polar_profile_read():
+    """(bp_ms, bp_launches, scl_ms, scl_launches) accumulated since the last read."""
+    a, b, c, d = _f64(0), _i32(0), _f64(0), _i32(0)
+    _check(load().polar_profile_read(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
+           "polar_profile_read")
+    return a.value, b.value, c.value, d.value
 
 
 def polar_hybrid_fallback_count(workspace, stream=None) -> int:

@@ -173,14 +173,105 @@ static size_t scl_scratch_bytes(int N, int L, int B)
     (void)B;
 }
 
+static size_t ws_bytes(const polar_code* code, int B, int L, int op);
+
+// One chunk's device buffers of hybrid_decode_host: LLRs, bits, status, iterations, hybrid
+// workspace; two such sets alternate.
+struct HostSet {
+    size_t llr, bits, status, iters, ws, ws_bytes, total;
+};
+static HostSet host_set_layout(const polar_code* code, int chunk, int L)
+{
+    HostSet h{};
+    const size_t row = (size_t)(code->K - code->crc_len + 7) / 8;
+    size_t o = 0;
+    h.llr = o;
+    o = align_up(o + (size_t)chunk * code->N * sizeof(float), 256);
+    h.bits = o;
+    o = align_up(o + (size_t)chunk * row, 256);
+    h.status = o;
+    o = align_up(o + (size_t)chunk, 256);
+    h.iters = o;
+    o = align_up(o + (size_t)chunk * sizeof(uint16_t), 256);
+    h.ws = o;
+    h.ws_bytes = ws_bytes(code, chunk, L, POLAR_OP_HYBRID);
+    o = align_up(o + h.ws_bytes, 256);
+    h.total = o;
+    return h;
+}
+
 static size_t ws_bytes(const polar_code* code, int B, int L, int op)
 {
     if (op == POLAR_OP_BP) return 0;
+    if (op == POLAR_OP_HYBRID_HOST) {
+        const int chunk = std::max(1, std::min(B, POLAR_HOST_CHUNK));
+        return 2 * host_set_layout(code, chunk, L).total;
+    }
     size_t b = kHeaderBytes;
     if (op == POLAR_OP_HYBRID) b += align_up(sizeof(int) * (size_t)std::max(B, 1), 256);
     b += scl_scratch_bytes(code->N, L, B);
     return b;
 }
+
+// library-owned second stream per device for hybrid_decode_host
+static std::mutex g_aux_mutex;
+static std::vector<cudaStream_t> g_aux;
+static int aux_stream(cudaStream_t* out)
+{
+    int dev = 0;
+    POLAR_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_aux_mutex);
+    if ((int)g_aux.size() <= dev) g_aux.resize(dev + 1, nullptr);
+    if (!g_aux[dev]) POLAR_CUDA(cudaStreamCreateWithFlags(&g_aux[dev], cudaStreamNonBlocking));
+    *out = g_aux[dev];
+    return POLAR_OK;
+}
+
+// ---------------------------------------------------------------------------- kernel timing
+struct ProfRecord {
+    int kind;  // 0 BP, 1 SCL
+    cudaEvent_t start, stop;
+};
+struct ProfState {
+    bool on = false;
+    std::vector<ProfRecord> recs;
+    std::vector<cudaEvent_t> pool;
+};
+static thread_local ProfState g_prof;
+
+static cudaEvent_t prof_event()
+{
+    if (!g_prof.pool.empty()) {
+        cudaEvent_t e = g_prof.pool.back();
+        g_prof.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one kernel launch with events when timing is enabled.
+struct ProfScope {
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t start = nullptr;
+    ProfScope(int k, cudaStream_t s) : kind(k), st(s)
+    {
+        if (g_prof.on) {
+            start = prof_event();
+            cudaEventRecord(start, st);
+        }
+    }
+    ~ProfScope()
+    {
+        if (start) {
+            cudaEvent_t stop = prof_event();
+            cudaEventRecord(stop, st);
+            g_prof.recs.push_back({kind, start, stop});
+        }
+    }
+};
 
 static int launch_bp(const DevCode* dcode, const polar_code* code, const float* llr, int B, int max_iters,
                      float llr_max, int precision, const float* w, int w_iters, uint8_t* bits, uint8_t* status,
@@ -225,6 +316,7 @@ static int launch_bp(const DevCode* dcode, const polar_code* code, const float* 
         return e == cudaSuccess ? POLAR_OK : cuda_fail(e, "bp_kernel launch");
     };
     if (B == 0) return POLAR_OK;
+    ProfScope prof(0, stream);
     switch (n) {
         case 7: return go(std::integral_constant<int, 7>{});
         case 8: return go(std::integral_constant<int, 8>{});
@@ -276,6 +368,7 @@ static int launch_scl(const DevCode* dcode, const polar_code* code, const float*
     a.next = next;
     a.scratch = static_cast<float*>(scratch);
     a.row_bytes = (code->K - code->crc_len + 7) / 8;
+    ProfScope prof(1, stream);
     const cudaError_t e = scl_launch(a, code->N, L, stream);
     return e == cudaSuccess ? POLAR_OK : cuda_fail(e, "scl_kernel launch");
 }
@@ -378,7 +471,7 @@ size_t polar_workspace_bytes(const polar_code* code, int32_t B, int32_t L, int32
 {
     if (check_code(code) != POLAR_OK || B < 0) return 0;
     if (op != POLAR_OP_BP && !valid_L(L)) return 0;
-    if (op < POLAR_OP_BP || op > POLAR_OP_HYBRID) return 0;
+    if (op < POLAR_OP_BP || op > POLAR_OP_HYBRID_HOST) return 0;
     return ws_bytes(code, B, L, op);
 }
 
@@ -440,6 +533,86 @@ int hybrid_decode(const polar_code* code, const float* llr, int32_t B, int32_t m
                         nullptr, nullptr, &h->fail_count, list, st)))
         return rc;
     return launch_scl(d, code, llr, B, L, bits, status, list, &h->fail_count, &h->scl_next, scratch, st);
+}
+
+int hybrid_decode_host(const polar_code* code, const float* llr_host, int32_t B, int32_t max_iters, float llr_max,
+                       int32_t precision, const float* wms_scales, int32_t wms_iters, int32_t L, uint8_t* bits_host,
+                       uint8_t* status_host, uint16_t* iters_host, void* workspace, size_t ws, void* stream)
+{
+    cudaStream_t st0 = static_cast<cudaStream_t>(stream);
+    int rc = check_bp_args(code, llr_host, B, max_iters, llr_max, precision, wms_scales, wms_iters, bits_host,
+                           status_host, iters_host);
+    if (rc) return rc;
+    if (!valid_L(L)) return fail(POLAR_ERR_ARG, "L = %d: must be 1, 2, 4, 8, 16 or 32", L);
+    const DevCode* d = nullptr;
+    if ((rc = code_slot(code, st0, &d))) return rc;
+    if (B == 0) return POLAR_OK;
+    const size_t need = ws_bytes(code, B, L, POLAR_OP_HYBRID_HOST);
+    if (!workspace || ws < need) return fail(POLAR_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws, need);
+    cudaStream_t st1 = nullptr;
+    if ((rc = aux_stream(&st1))) return rc;
+    const int chunk = std::min(B, POLAR_HOST_CHUNK);
+    const HostSet hs = host_set_layout(code, chunk, L);
+    const size_t N = (size_t)code->N, row = (size_t)(code->K - code->crc_len + 7) / 8;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    POLAR_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+    POLAR_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+    POLAR_CUDA(cudaEventRecord(ev_in, st0));
+    POLAR_CUDA(cudaStreamWaitEvent(st1, ev_in, 0));
+    const cudaStream_t sts[2] = {st0, st1};
+    for (int c = 0, b0 = 0; b0 < B; ++c, b0 += chunk) {
+        const int nb = std::min(chunk, B - b0);
+        const cudaStream_t st = sts[c & 1];
+        char* base = static_cast<char*>(workspace) + (size_t)(c & 1) * hs.total;
+        float* llr_d = reinterpret_cast<float*>(base + hs.llr);
+        uint8_t* bits_d = reinterpret_cast<uint8_t*>(base + hs.bits);
+        uint8_t* status_d = reinterpret_cast<uint8_t*>(base + hs.status);
+        uint16_t* iters_d = reinterpret_cast<uint16_t*>(base + hs.iters);
+        POLAR_CUDA(cudaMemcpyAsync(llr_d, llr_host + (size_t)b0 * N, (size_t)nb * N * sizeof(float),
+                                   cudaMemcpyHostToDevice, st));
+        rc = hybrid_decode(code, llr_d, nb, max_iters, llr_max, precision, wms_scales, wms_iters, L, bits_d, status_d,
+                           iters_d, base + hs.ws, hs.ws_bytes, st);
+        if (rc) break;
+        if (row) POLAR_CUDA(cudaMemcpyAsync(bits_host + (size_t)b0 * row, bits_d, (size_t)nb * row,
+                                            cudaMemcpyDeviceToHost, st));
+        POLAR_CUDA(cudaMemcpyAsync(status_host + b0, status_d, (size_t)nb, cudaMemcpyDeviceToHost, st));
+        POLAR_CUDA(cudaMemcpyAsync(iters_host + b0, iters_d, (size_t)nb * sizeof(uint16_t), cudaMemcpyDeviceToHost,
+                                   st));
+    }
+    POLAR_CUDA(cudaEventRecord(ev_out, st1));
+    POLAR_CUDA(cudaStreamWaitEvent(st0, ev_out, 0));
+    cudaEventDestroy(ev_in);
+    cudaEventDestroy(ev_out);
+    return rc;
+}
+
+int polar_profile_enable(int32_t on)
+{
+    g_prof.on = on != 0;
+    return POLAR_OK;
+}
+
+int polar_profile_read(double* bp_ms, int32_t* bp_launches, double* scl_ms, int32_t* scl_launches)
+{
+    double t[2] = {0.0, 0.0};
+    int cnt[2] = {0, 0};
+    int rc = POLAR_OK;
+    for (const ProfRecord& r : g_prof.recs) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(r.stop);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.start, r.stop);
+        if (e != cudaSuccess && rc == POLAR_OK) rc = cuda_fail(e, "polar_profile_read");
+        t[r.kind] += ms;
+        cnt[r.kind] += 1;
+        g_prof.pool.push_back(r.start);
+        g_prof.pool.push_back(r.stop);
+    }
+    g_prof.recs.clear();
+    if (bp_ms) *bp_ms = t[0];
+    if (bp_launches) *bp_launches = cnt[0];
+    if (scl_ms) *scl_ms = t[1];
+    if (scl_launches) *scl_launches = cnt[1];
+    return rc;
 }
 
 int polar_hybrid_fallback_count(const void* workspace, int32_t* out, void* stream)

@@ -228,7 +228,7 @@ def test_hybrid_full_size_sampled():
 
 def test_encoder_bit_exact():
     for N, K, crc in [(128, 64, 8), (256, 100, 16), (1024, 512, 16), (2048, 1024, 24), (512, 24, 24)]:
-        ocode = fr.oracle_code(N, K, crc)
+        ocode = fr.oracle_code(N, K, crc, design_rate=K / N)
         code = fr.api_code(ocode)
         from paper_1609_09358_gb300 import inputs
         pay = inputs.payload_bits(9, 0, 67, ocode.P)
@@ -254,3 +254,39 @@ def test_generators_match_cpu_stream():
     z = inputs.unit_noise(99, 5, B, N)
     ref = 2.0 * ((1.0 - 2.0 * x) + sigma * z) / sigma ** 2
     assert np.allclose(llr.cpu().numpy(), ref, rtol=1e-4, atol=1e-4)
+
+
+def test_hybrid_host_buffers_match_device_path():
+    """hybrid_decode_host over several chunks (and a ragged last chunk) equals hybrid_decode."""
+    ocode = fr.oracle_code(128, 64, 8)
+    code = fr.api_code(ocode)
+    B = 70_001
+    _, llr = fr.frames_large(ocode, 1.5, B, seed=88)
+    dec = api.Decoder(code, B, 4)
+    dec.hybrid(dev(llr), 50, 20.0)
+    torch.cuda.synchronize()
+    bits_h = torch.zeros((B, code.row_bytes), dtype=torch.uint8).pin_memory()
+    status_h = torch.zeros(B, dtype=torch.uint8).pin_memory()
+    iters_h = torch.zeros(B, dtype=torch.int16).pin_memory()
+    ws = torch.zeros(api.polar_workspace_bytes(code, B, 4, api.POLAR_OP_HYBRID_HOST), dtype=torch.uint8,
+                     device="cuda")
+    api.hybrid_decode_host(code, torch.from_numpy(llr).pin_memory(), 50, 20.0, api.POLAR_FP32, None, 4, bits_h,
+                           status_h, iters_h, ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(bits_h.numpy(), dec.bits.cpu().numpy())
+    assert np.array_equal(status_h.numpy(), dec.status.cpu().numpy())
+    assert np.array_equal(iters_h.numpy(), dec.iters.cpu().numpy())
+
+
+def test_profiling_hooks_count_launches():
+    ocode = fr.oracle_code(256, 128, 16)
+    code = fr.api_code(ocode)
+    _, llr = fr.frames(ocode, 1.0, 64, seed=3)
+    dec = api.Decoder(code, 64, 8)
+    api.polar_profile_enable(True)
+    for _ in range(3):
+        dec.hybrid(dev(llr), 20, 20.0)
+    api.polar_profile_enable(False)
+    bp_ms, bp_n, scl_ms, scl_n = api.polar_profile_read()
+    assert bp_n == 3 and scl_n == 3 and bp_ms > 0 and scl_ms > 0
+    assert api.polar_profile_read()[1] == 0
