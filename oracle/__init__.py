@@ -211,8 +211,9 @@ def build_u(payload, code: Code) -> np.ndarray:
 
 def encode_batch(payload, code: Code) -> np.ndarray:
     """payload uint8 [B][P] (one byte per bit) -> codeword uint8 [B][N] (matrix definition)."""
-    payload = _u8(payload).reshape(-1, code.P)
-    B = payload.shape[0]
+    payload = _u8(payload)
+    B = payload.shape[0] if payload.ndim == 2 else payload.size // max(code.P, 1)
+    payload = payload.reshape(B, code.P)
     x = np.zeros((B, code.N), np.uint8)
     lib().or_encode_batch(_p(payload, _u8p), B, code.N, code.K, _p(code.info_idx, _i32p),
                           code.crc_poly, code.crc_len, _p(x, _u8p))
