@@ -168,6 +168,29 @@ int hybrid_decode_host(const polar_code* code, const float* llr_host, int32_t B,
 int polar_profile_enable(int32_t on);
 int polar_profile_read(double* bp_ms, int32_t* bp_launches, double* scl_ms, int32_t* scl_launches);
 
+/* hybrid_decode without any device allocation (the paper has no counterpart: this exists for
+ * callers that cannot allocate device memory -- for instance a receive chain that must never call
+ * cudaMalloc once running, because an allocation can synchronise the device and take unbounded
+ * time, or a plug-in whose host application owns and budgets all device memory).  It decodes like
+ * hybrid_decode but takes no workspace: its scratch (two counters and the list of frames that go
+ * to CA-SCL) is one static device array of about 256 KB inside this library, which every GPU that
+ * loads the library holds until the process exits.
+ *   Limits: B <= POLAR_NOALLOC_MAX_FRAMES, and the CA-SCL list must fit in shared memory
+ *   (L (N - 2) 4 bytes <= 72 KiB, e.g. N = 1024 with L <= 16); larger requests return
+ *   POLAR_ERR_ARG with a message.
+ *   The first call on a device looks up the array's device address (and, like every first use of
+ *   a code, uploads the code tables); make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents; the counters are cleared on
+ *   `stream` at the start of every call.  Calls that overlap on the GPU (different streams, or
+ *   different host threads) race on the array and must be serialised by the caller.
+ *   Nothing here calls cudaMalloc, cudaFree or any allocating routine.  Other arguments as in
+ *   hybrid_decode. */
+#define POLAR_NOALLOC_MAX_FRAMES 65536
+int hybrid_decode_noalloc(const polar_code* code, const float* llr, int32_t B, int32_t max_iters,
+                          float llr_max, int32_t precision, const float* wms_scales,
+                          int32_t wms_iters, int32_t L, uint8_t* bits, uint8_t* status,
+                          uint16_t* iters, void* stream);
+
 /* Device workspace needed by an operation (op = POLAR_OP_*) on B frames with list size L
  * (ignored for POLAR_OP_BP).  Returns 0 on invalid arguments as well as when none is needed. */
 size_t polar_workspace_bytes(const polar_code* code, int32_t B, int32_t L, int32_t op);

@@ -50,6 +50,8 @@ SIGNATURES = {
                                      _vp]),
     "hybrid_decode_host": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _i32, _vp, _i32, _i32, _vp, _vp, _vp, _vp,
                                           _sz, _vp]),
+    "hybrid_decode_noalloc": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _i32, _vp, _i32, _i32, _vp, _vp, _vp,
+                                             _vp]),
     "polar_profile_enable": (ctypes.c_int, [_i32]),
     "polar_profile_read": (ctypes.c_int, [ctypes.POINTER(_f64), ctypes.POINTER(_i32), ctypes.POINTER(_f64),
                                           ctypes.POINTER(_i32)]),
@@ -208,6 +210,18 @@ def hybrid_decode_host(code: PolarCode, llr_host, max_iters: int, llr_max: float
                                      _ptr(wms_scales), w_iters, L, bits_host.data_ptr(), status_host.data_ptr(),
                                      iters_host.data_ptr(), _ptr(workspace), ws_b, _stream(stream)),
            "hybrid_decode_host")
+
+
+def hybrid_decode_noalloc(code: PolarCode, llr, max_iters: int, llr_max: float, precision: int, wms_scales,
+                          L: int, bits, status, iters, stream=None) -> None:
+    """hybrid_decode for callers that cannot allocate device memory: no workspace argument; the
+    library's static scratch array is used instead (B <= 65536 frames, CA-SCL list in shared
+    memory).  Calls that overlap on the GPU race on that array."""
+    B = llr.shape[0]
+    w_iters = 0 if wms_scales is None else int(wms_scales.shape[0])
+    _check(load().hybrid_decode_noalloc(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, _ptr(wms_scales),
+                                        w_iters, L, _ptr(bits), _ptr(status), _ptr(iters), _stream(stream)),
+           "hybrid_decode_noalloc")
 
 
 def polar_profile_enable(on: bool) -> None:

@@ -627,3 +627,68 @@ int polar_hybrid_fallback_count(const void* workspace, int32_t* out, void* strea
 }
 
 }  // extern "C"
+
+// ==================================================================================== no-alloc
+// hybrid_decode_noalloc: the hybrid decoder for callers that cannot allocate device memory.  Its
+// scratch (the two work counters and the list of frames that fall back to CA-SCL) lives in the
+// file-scope array below, which every GPU that loads this library holds until the process exits.
+namespace polar {
+
+constexpr size_t kNoallocScratchBytes = kHeaderBytes + sizeof(int) * (size_t)POLAR_NOALLOC_MAX_FRAMES;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+static std::mutex g_noalloc_mutex;
+static std::vector<void*> g_noalloc_ptr;  // device address of g_noalloc_scratch, per device
+
+// Device address of the static scratch on the current device.  Host code cannot pass the
+// array's name to a kernel (on the host it names a host-side stand-in), so the address is looked
+// up once per device with that device current.
+static int noalloc_scratch(void** out)
+{
+    int dev = 0;
+    POLAR_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if ((int)g_noalloc_ptr.size() <= dev) g_noalloc_ptr.resize(dev + 1, nullptr);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return POLAR_OK;
+}
+
+}  // namespace polar
+
+extern "C" int hybrid_decode_noalloc(const polar_code* code, const float* llr, int32_t B, int32_t max_iters,
+                                     float llr_max, int32_t precision, const float* wms_scales, int32_t wms_iters,
+                                     int32_t L, uint8_t* bits, uint8_t* status, uint16_t* iters, void* stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_bp_args(code, llr, B, max_iters, llr_max, precision, wms_scales, wms_iters, bits, status, iters);
+    if (rc) return rc;
+    if (!valid_L(L)) return fail(POLAR_ERR_ARG, "L = %d: must be 1, 2, 4, 8, 16 or 32", L);
+    if (B > POLAR_NOALLOC_MAX_FRAMES)
+        return fail(POLAR_ERR_ARG, "hybrid_decode_noalloc: B = %d exceeds the static limit of %d frames per call", B,
+                    POLAR_NOALLOC_MAX_FRAMES);
+    if (!scl_fits_smem(code->N, L))
+        return fail(POLAR_ERR_ARG,
+                    "hybrid_decode_noalloc: the CA-SCL list of N = %d, L = %d needs device scratch beyond the "
+                    "static array; use hybrid_decode with a workspace",
+                    code->N, L);
+    const DevCode* d = nullptr;
+    if ((rc = code_slot(code, st, &d))) return rc;
+    if (B == 0) return POLAR_OK;
+    void* scratch = nullptr;
+    if ((rc = noalloc_scratch(&scratch))) return rc;
+    char* base = static_cast<char*>(scratch);
+    WsHeader* h = reinterpret_cast<WsHeader*>(base);
+    int* list = reinterpret_cast<int*>(base + kHeaderBytes);
+    // the array keeps the previous call's counters: they must start at zero
+    POLAR_CUDA(cudaMemsetAsync(h, 0, sizeof(WsHeader), st));
+    if ((rc = launch_bp(d, code, llr, B, max_iters, llr_max, precision, wms_scales, wms_iters, bits, status, iters,
+                        nullptr, nullptr, &h->fail_count, list, st)))
+        return rc;
+    return launch_scl(d, code, llr, B, L, bits, status, list, &h->fail_count, &h->scl_next, nullptr, st);
+}
