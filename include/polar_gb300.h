@@ -175,9 +175,9 @@ int polar_profile_read(double* bp_ms, int32_t* bp_launches, double* scl_ms, int3
  * hybrid_decode but takes no workspace: its scratch (two counters and the list of frames that go
  * to CA-SCL) is one static device array of about 256 KB inside this library, which every GPU that
  * loads the library holds until the process exits.
- *   Limits: B <= POLAR_NOALLOC_MAX_FRAMES, and the CA-SCL list must fit in shared memory
- *   (L (N - 2) 4 bytes <= 72 KiB, e.g. N = 1024 with L <= 16); larger requests return
- *   POLAR_ERR_ARG with a message.
+ *   Limits: B <= POLAR_NOALLOC_MAX_FRAMES, and one frame's CA-SCL list (its LLR and
+ *   partial-sum arrays, about 4 L N bytes) must fit in 80 KiB of shared memory, e.g. N = 1024
+ *   with L <= 16; larger requests return POLAR_ERR_ARG with a message.
  *   The first call on a device looks up the array's device address (and, like every first use of
  *   a code, uploads the code tables); make that first call before any stream capture.
  *   All calls share the array and it keeps the last call's contents; the counters are cleared on

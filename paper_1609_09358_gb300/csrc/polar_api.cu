@@ -166,13 +166,6 @@ constexpr size_t kHeaderBytes = 256;
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-static size_t scl_scratch_bytes(int N, int L, int B)
-{
-    if (scl_fits_smem(N, L)) return 0;
-    return (size_t)scl_resident_warps(N, L) * scl_global_warp_bytes(N, L);
-    (void)B;
-}
-
 static size_t ws_bytes(const polar_code* code, int B, int L, int op);
 
 // One chunk's device buffers of hybrid_decode_host: LLRs, bits, status, iterations, hybrid
@@ -209,7 +202,7 @@ static size_t ws_bytes(const polar_code* code, int B, int L, int op)
     }
     size_t b = kHeaderBytes;
     if (op == POLAR_OP_HYBRID) b += align_up(sizeof(int) * (size_t)std::max(B, 1), 256);
-    b += scl_scratch_bytes(code->N, L, B);
+    b += scl_scratch_bytes(code->N, L);
     return b;
 }
 
@@ -434,7 +427,7 @@ int polar_encode(const polar_code* code, const uint8_t* payload, int32_t B, uint
     int rc = code_slot(code, st, &d);
     if (rc) return rc;
     if (B == 0) return POLAR_OK;
-    if (!payload || !codeword) return fail(POLAR_ERR_ARG, "NULL payload/codeword");
+    if (!codeword || (!payload && code->K > code->crc_len)) return fail(POLAR_ERR_ARG, "NULL payload/codeword");
     const int warps = 4;
     encode_kernel<<<(B + warps - 1) / warps, warps * 32, 0, st>>>(d, payload, B, (code->K - code->crc_len + 7) / 8,
                                                                 codeword);

@@ -13,17 +13,23 @@
 // by the index tie-break -- and the rank < L candidates survive, renumbered in ascending index.
 //
 // Lazy copy: every level k keeps L physical LLR arrays and L physical partial-sum arrays; a path
-// holds one pointer per level.  A surviving child copies only its parent's pointer row.  Since a
-// level is always rewritten whole, a path that is about to write a level it shares takes a free
-// array of that level instead (the lowest-numbered sharer keeps the old one): no LLR or
-// partial-sum data is ever copied.  A level is checked only if a list step duplicated a path since
-// it was last written.
+// holds one 5-bit pointer per level, packed into two registers per table (lane = path).  A
+// surviving child copies only its parent's pointer words (four shuffles).  Since a level is always
+// rewritten whole, a path that is about to write a level it shares takes a free array of that
+// level instead (the lowest-numbered sharer keeps the old one): no LLR or partial-sum data is ever
+// copied.  A level is checked only if a list step duplicated a path since it was last written.
 //
 // Partial sums: after deciding bit i, the completed subtree re-encodes bottom-up,
 // v_{k+1} = (C_k xor v_k) || v_k, until the first level k where the completed node is a left
 // child (k = number of trailing ones of i); v_k is stored there.  After the last bit the level-n
 // array holds the path's codeword x, and u = x G (G is an involution) gives the decided bits for
 // the CRC check and the output.
+//
+// Storage: the small, hot levels (LLR levels 1..KS, partial sums 0..KC) sit in the warp's slice
+// of shared memory; the large upper levels, touched once per 2^k bits, sit in the warp's slot of
+// the global workspace (L2-resident).  This keeps ~10 KB of shared memory per warp, so that many
+// frames are in flight per SM -- the decoder is latency-bound (serial over the N bits).  With no
+// workspace every level is in shared memory (KS = n-1, KC = n).
 #pragma once
 
 #include <algorithm>
@@ -42,38 +48,50 @@ struct SCLArgs {
     const int* list;   // frame indices to decode (null: 0..B-1)
     const int* count;  // device count of `list` (null: B)
     int* next;         // work counter, zero before the launch
-    float* scratch;    // per-warp LLR arrays when they do not fit shared memory
+    float* scratch;    // per-warp slots of the global levels (null: all levels in shared memory)
     int row_bytes;
+    int KS, KC;        // last LLR / partial-sum level kept in shared memory
+    int warp_words;    // shared-memory words per warp
+    long long slot_words;  // global words per warp
 };
 
 __host__ __device__ inline int scl_cw(int k) { return k < 5 ? 1 : 1 << (k - 5); }  // words of a level-k C array
-__host__ __device__ inline int scl_coff(int k, int L)  // word offset of level k's C arrays
-{
-    int s = 0;
-    for (int q = 0; q < k; ++q) s += scl_cw(q);
-    return s * L;
-}
-__host__ __device__ inline int scl_aoff(int k, int L) { return L * ((1 << k) - 2); }  // float offset, k >= 1
+__host__ __device__ inline int scl_cwsum(int k) { return k <= 5 ? k : 4 + (1 << (k - 5)); }  // sum of cw(q), q < k
 
-// per-warp shared memory: C arrays (levels 0..n) | pointer rows A and C [n+1][32] | candidate
-// slots [64] | LLR arrays (levels 1..n-1) when resident
-__host__ __device__ inline int scl_small_words(int n, int L) { return scl_coff(n + 1, L) + (2 * (n + 1) * 32 + 64) / 4; }
-inline size_t scl_llr_bytes(int N, int L) { return (size_t)L * (N - 2) * sizeof(float); }
 inline int log2_host(int v)
 {
     int n = 0;
     while ((1 << n) < v) ++n;
     return n;
 }
-inline bool scl_fits_smem(int N, int L) { return scl_llr_bytes(N, L) <= 72 * 1024; }
-inline size_t scl_warp_smem_bytes(int N, int L)
+
+// Host plan of the shared/global split for (N, L).
+struct SCLPlan {
+    int KS, KC;
+    int warp_words;
+    long long slot_words;
+};
+inline SCLPlan scl_plan(int N, int L, bool all_smem)
 {
-    size_t b = (size_t)scl_small_words(log2_host(N), L) * 4;
-    b = (b + 15) / 16 * 16;
-    if (scl_fits_smem(N, L)) b += scl_llr_bytes(N, L);
-    return b;
+    const int n = log2_host(N);
+    SCLPlan p{};
+    if (all_smem) {
+        p.KS = n - 1;
+        p.KC = n;
+    } else {
+        p.KS = 1;
+        while (p.KS + 1 <= n - 1 && 4LL * L * ((2 << (p.KS + 1)) - 2) <= 8192) ++p.KS;
+        p.KC = 0;
+        while (p.KC + 1 <= n && 4LL * L * scl_cwsum(p.KC + 2) <= 3072) ++p.KC;
+    }
+    p.warp_words = L * scl_cwsum(p.KC + 1) + L * ((2 << p.KS) - 2) + 16;
+    p.warp_words = (p.warp_words + 3) & ~3;
+    p.slot_words = (long long)L * (N - (2 << p.KS)) + (long long)L * (scl_cwsum(n + 1) - scl_cwsum(p.KC + 1));
+    return p;
 }
-constexpr int kSclGlobalWarpsPerSM = 8;
+inline bool scl_fits_smem(int N, int L) { return 4LL * scl_plan(N, L, true).warp_words <= 80 * 1024; }
+constexpr int kSclWarpsPerSM = 32;
+constexpr int kSclWarpsPerCTA = 4;
 inline int scl_sm_count()
 {
     int dev = 0, sms = 0;
@@ -81,172 +99,211 @@ inline int scl_sm_count()
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return sms > 0 ? sms : 1;
 }
-inline size_t scl_resident_warps(int N, int L) { return (size_t)scl_sm_count() * kSclGlobalWarpsPerSM; }
-inline size_t scl_global_warp_bytes(int N, int L) { return scl_llr_bytes(N, L); }
+// global workspace of the SCL list arrays (one slot per resident warp)
+inline size_t scl_scratch_bytes(int N, int L)
+{
+    const SCLPlan p = scl_plan(N, L, false);
+    return (size_t)scl_sm_count() * kSclWarpsPerSM * (size_t)p.slot_words * 4;
+}
 
-// A path about to rewrite level row[] that it shares takes a free array of that level.  Lanes
-// are paths; `active` paths.  The lowest lane of each group of sharers keeps its array.
-__device__ __forceinline__ void scl_own(uint8_t* row, int active, int L)
+__device__ __forceinline__ uint32_t fld(const uint32_t (&w)[2], int k) { return ((k < 6 ? w[0] : w[1]) >> (5 * (k % 6))) & 31u; }
+__device__ __forceinline__ void set_fld(uint32_t (&w)[2], int k, uint32_t v)
+{
+    const int s = 5 * (k % 6);
+    if (k < 6)
+        w[0] = (w[0] & ~(31u << s)) | (v << s);
+    else
+        w[1] = (w[1] & ~(31u << s)) | (v << s);
+}
+
+// A path about to rewrite level k that it shares takes a free array of that level (lane = path;
+// `act` active paths; the lowest lane of each group of sharers keeps its array).
+__device__ __forceinline__ void scl_own(uint32_t (&w)[2], int k, int act, int L)
 {
     const int lane = threadIdx.x & 31;
-    const bool act = lane < active;
-    const int mine = act ? row[lane] : 64 + lane;
+    const bool on = lane < act;
+    const uint32_t mine = on ? fld(w, k) : 64u + lane;
     const uint32_t same = __match_any_sync(0xffffffffu, mine);
-    const bool need = act && (same & ((1u << lane) - 1u)) != 0u;
-    const uint32_t used = __reduce_or_sync(0xffffffffu, act ? (1u << mine) : 0u);
-    const uint32_t all = L >= 32 ? 0xffffffffu : ((1u << L) - 1u);
-    uint32_t freem = ~used & all;
-    const uint32_t needm = __ballot_sync(0xffffffffu, need);
-    const int r = __popc(needm & ((1u << lane) - 1u));
+    const uint32_t below = (1u << lane) - 1u;
+    const bool need = on && (same & below) != 0u;
+    const uint32_t used = __reduce_or_sync(0xffffffffu, on ? (1u << mine) : 0u);
+    uint32_t freem = ~used & (L >= 32 ? 0xffffffffu : ((1u << L) - 1u));
+    const int r = __popc(__ballot_sync(0xffffffffu, need) & below);
     if (need) {
         for (int q = 0; q < r; ++q) freem &= freem - 1u;  // drop the r lowest free arrays
-        row[lane] = (uint8_t)(__ffs(freem) - 1);
+        set_fld(w, k, (uint32_t)(__ffs(freem) - 1));
     }
-    __syncwarp();
 }
 
 __device__ __forceinline__ float scl_g(float a, float b, uint32_t v) { return v ? __fsub_rn(b, a) : __fadd_rn(b, a); }
 
-__device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, uint32_t* cb, uint8_t* ptrA,
-                                 uint8_t* ptrC, uint8_t* selc, float* A)
+struct SCLWarp {
+    float* sA;     // shared LLR levels 1..KS
+    uint32_t* sC;  // shared partial-sum levels 0..KC
+    float* gA;     // global LLR levels KS+1..n-1
+    uint32_t* gC;  // global partial-sum levels KC+1..n
+    int L, KS, KC;
+    __device__ __forceinline__ float* A(int k) const
+    {
+        return k <= KS ? sA + L * ((1 << k) - 2) : gA + L * ((1 << k) - (2 << KS));
+    }
+    __device__ __forceinline__ uint32_t* Cl(int k) const
+    {
+        return k <= KC ? sC + L * scl_cwsum(k) : gC + L * (scl_cwsum(k) - scl_cwsum(KC + 1));
+    }
+};
+
+template <bool TWO>  // TWO: L = 32, two candidates per lane
+__device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, const SCLWarp& S, uint8_t* selc)
 {
     const int lane = threadIdx.x & 31;
     const int N = C.N, n = C.n, L = a.L;
     const float* y = a.llr + (size_t)frame * N;
-    for (int k = 0; k <= n; ++k) {
-        ptrA[k * 32 + lane] = 0;
-        ptrC[k * 32 + lane] = 0;
-    }
-    __syncwarp();
+    uint32_t pA[2] = {0u, 0u}, pC[2] = {0u, 0u};  // pointer rows of path `lane`
     float pm = 0.0f, lam = 0.0f;
     int act = 1;
     uint32_t shA = 0u, shC = 0u;  // levels that may be shared since the last duplication
+    uint32_t fw = 0u;
     for (int i = 0; i < N; ++i) {
+        if ((i & 31) == 0) fw = C.frozen_bits[i >> 5];
         const int t = i == 0 ? n : __ffs(i) - 1;
         const int top = i == 0 ? n - 1 : t;
         for (int k = top; k >= 1; --k) {
             if ((shA >> k) & 1u) {
-                scl_own(ptrA + k * 32, act, L);
+                scl_own(pA, k, act, L);
                 shA &= ~(1u << k);
             }
             const bool use_g = i != 0 && k == t;
+            const bool from_ch = k + 1 == n;
             const int len = 1 << k;
-            float* dstbase = A + scl_aoff(k, L);
-            for (int e = lane; e < (act << k); e += 32) {
-                const int p = e >> k, j = e & (len - 1);
-                const float* src = (k + 1 == n) ? y : A + scl_aoff(k + 1, L) + ptrA[(k + 1) * 32 + p] * (2 * len);
-                const float va = src[j], vb = src[j + len];
-                float r;
-                if (use_g) {
-                    const uint32_t w = cb[scl_coff(k, L) + ptrC[k * 32 + p] * scl_cw(k) + (j >> 5)];
-                    r = scl_g(va, vb, (w >> (j & 31)) & 1u);
-                } else {
-                    r = xmin(va, vb);
+            float* dst = S.A(k);
+            const float* srcb = from_ch ? y : S.A(k + 1);
+            const uint32_t* cbk = S.Cl(k);
+            const uint32_t my_d = fld(pA, k), my_s = from_ch ? 0u : fld(pA, k + 1), my_c = fld(pC, k);
+            const int cwk = scl_cw(k), total = act << k;
+            for (int e0 = 0; e0 < total; e0 += 32) {
+                const int e = e0 + lane;
+                const int p = (e >> k) & 31;
+                const uint32_t pd = __shfl_sync(0xffffffffu, my_d, p);
+                const uint32_t ps = __shfl_sync(0xffffffffu, my_s, p);
+                const uint32_t pc = __shfl_sync(0xffffffffu, my_c, p);
+                if (e < total) {
+                    const int j = e & (len - 1);
+                    const float* src = srcb + ps * (2 * len);
+                    const float va = src[j], vb = src[j + len];
+                    float r;
+                    if (use_g) {
+                        const uint32_t w = cbk[pc * cwk + (j >> 5)];
+                        r = scl_g(va, vb, (w >> (j & 31)) & 1u);
+                    } else {
+                        r = xmin(va, vb);
+                    }
+                    dst[pd * len + j] = r;
                 }
-                dstbase[ptrA[k * 32 + p] * len + j] = r;
             }
             __syncwarp();
         }
         // bit LLR (level 0), lane = path
         if (lane < act) {
-            const float* src = A + scl_aoff(1, L) + ptrA[32 + lane] * 2;
+            const float* src = S.A(1) + fld(pA, 1) * 2;
             const float va = src[0], vb = src[1];
             if (i != 0 && t == 0)
-                lam = scl_g(va, vb, cb[scl_coff(0, L) + ptrC[lane]] & 1u);
+                lam = scl_g(va, vb, S.Cl(0)[fld(pC, 0)] & 1u);
             else
                 lam = xmin(va, vb);
         }
         uint32_t bitv = 0u;
-        if (frozen_at(C.frozen_bits, i)) {
+        if ((fw >> (i & 31)) & 1u) {
             if (lane < act && lam < 0.0f) pm = __fadd_rn(pm, fabsf(lam));
         } else {
             // ---------------------------------------------------------------- list step
             const int nc = 2 * act;
-            const int cpl = nc > 32 ? 2 : 1;  // candidates per lane
-            float cm[2];
-            bool valid[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c = lane + 32 * h;
-                const float lp = __shfl_sync(0xffffffffu, lam, (c >> 1) & 31);
-                const float pp = __shfl_sync(0xffffffffu, pm, (c >> 1) & 31);
-                valid[h] = h < cpl && c < nc;
-                const uint32_t b = c & 1;
-                cm[h] = (b != (uint32_t)(lp < 0.0f)) ? __fadd_rn(pp, fabsf(lp)) : pp;
+            float cm0, cm1 = 0.0f;
+            {
+                const float lp = __shfl_sync(0xffffffffu, lam, (lane >> 1) & 31);
+                const float pp = __shfl_sync(0xffffffffu, pm, (lane >> 1) & 31);
+                cm0 = ((uint32_t)(lane & 1) != (uint32_t)(lp < 0.0f)) ? __fadd_rn(pp, fabsf(lp)) : pp;
             }
-            int rank[2] = {0, 0};
-            for (int c2 = 0; c2 < nc; ++c2) {
-                const float o = __shfl_sync(0xffffffffu, c2 < 32 ? cm[0] : cm[1], c2 & 31);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int c = lane + 32 * h;
-                    rank[h] += (o < cm[h]) || (o == cm[h] && c2 < c);
+            if constexpr (TWO) {
+                const float lp = __shfl_sync(0xffffffffu, lam, 16 + (lane >> 1));
+                const float pp = __shfl_sync(0xffffffffu, pm, 16 + (lane >> 1));
+                cm1 = ((uint32_t)(lane & 1) != (uint32_t)(lp < 0.0f)) ? __fadd_rn(pp, fabsf(lp)) : pp;
+            }
+            int rank0 = 0, rank1 = 0;
+            const int n0 = nc < 32 ? nc : 32;
+            for (int c2 = 0; c2 < n0; ++c2) {
+                const float o = __shfl_sync(0xffffffffu, cm0, c2);
+                rank0 += (o < cm0) || (o == cm0 && c2 < lane);
+                if constexpr (TWO) rank1 += o <= cm1;  // every c2 < 32 precedes candidate lane + 32 on ties
+            }
+            if constexpr (TWO) {
+                for (int c2 = 32; c2 < nc; ++c2) {
+                    const float o = __shfl_sync(0xffffffffu, cm1, c2 - 32);
+                    rank0 += o < cm0;
+                    rank1 += (o < cm1) || (o == cm1 && c2 < lane + 32);
                 }
             }
-            const uint32_t km0 = __ballot_sync(0xffffffffu, valid[0] && rank[0] < L);
-            const uint32_t km1 = __ballot_sync(0xffffffffu, valid[1] && rank[1] < L);
             const uint32_t below = (1u << lane) - 1u;
+            const uint32_t km0 = __ballot_sync(0xffffffffu, lane < nc && rank0 < L);
+            const uint32_t km1 = TWO ? __ballot_sync(0xffffffffu, lane + 32 < nc && rank1 < L) : 0u;
             if (km0 & (1u << lane)) selc[__popc(km0 & below)] = (uint8_t)lane;
-            if (km1 & (1u << lane)) selc[__popc(km0) + __popc(km1 & below)] = (uint8_t)(lane + 32);
+            if (TWO && (km1 & (1u << lane))) selc[__popc(km0) + __popc(km1 & below)] = (uint8_t)(lane + 32);
             const bool dup = ((km0 & (km0 >> 1) & 0x55555555u) | (km1 & (km1 >> 1) & 0x55555555u)) != 0u;
             const int nact = __popc(km0) + __popc(km1);
             __syncwarp();
-            int cq = 0;
-            if (lane < nact) cq = selc[lane];
-            const float m0 = __shfl_sync(0xffffffffu, cm[0], cq & 31);
-            const float m1 = __shfl_sync(0xffffffffu, cm[1], cq & 31);
+            const int cq = lane < nact ? selc[lane] : 0;
+            __syncwarp();
+            const float m0 = __shfl_sync(0xffffffffu, cm0, cq & 31);
+            const float m1 = TWO ? __shfl_sync(0xffffffffu, cm1, cq & 31) : 0.0f;
             const int parent = cq >> 1;
             bitv = (uint32_t)(cq & 1);
-            // pointer rows of the survivors: copies of their parents' rows
-            uint8_t ra[12], rc[12];
-#pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                if (k <= n && lane < nact) {
-                    ra[k] = ptrA[k * 32 + parent];
-                    rc[k] = ptrC[k * 32 + parent];
-                }
-            }
-            __syncwarp();
-#pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                if (k <= n && lane < nact) {
-                    ptrA[k * 32 + lane] = ra[k];
-                    ptrC[k * 32 + lane] = rc[k];
-                }
-            }
+            // pointer rows of the survivors: their parents' rows
+            pA[0] = __shfl_sync(0xffffffffu, pA[0], parent);
+            pA[1] = __shfl_sync(0xffffffffu, pA[1], parent);
+            pC[0] = __shfl_sync(0xffffffffu, pC[0], parent);
+            pC[1] = __shfl_sync(0xffffffffu, pC[1], parent);
             pm = lane < nact ? (cq < 32 ? m0 : m1) : 0.0f;
             act = nact;
             if (dup) shA = shC = 0xffffffffu;
-            __syncwarp();
         }
         // -------------------------------------------------------------- partial sums
         const int kc = __ffs(~i) - 1;  // trailing ones of i; n after the last bit
         if ((shC >> kc) & 1u) {
-            scl_own(ptrC + kc * 32, act, L);
+            scl_own(pC, kc, act, L);
             shC &= ~(1u << kc);
         }
         {
+            uint32_t* dstl = S.Cl(kc);
+            const int cwk = scl_cw(kc);
             // bottom five levels in one word per path (lane = path)
             uint32_t v = bitv;
             const int kw = kc < 5 ? kc : 5;
             if (lane < act) {
                 for (int k = 0; k < kw; ++k) {
-                    const uint32_t ck = cb[scl_coff(k, L) + ptrC[k * 32 + lane] * scl_cw(k)];
+                    const uint32_t ck = S.Cl(k)[fld(pC, k)];
                     const uint32_t m = (1u << (1 << k)) - 1u;
                     v = ((v ^ ck) & m) | ((v & m) << (1 << k));
                 }
-                cb[scl_coff(kc, L) + ptrC[kc * 32 + lane] * scl_cw(kc)] = v;
+                dstl[fld(pC, kc) * cwk] = v;
             }
             __syncwarp();
+            const uint32_t my_dst = fld(pC, kc);
             for (int k = 5; k < kc; ++k) {
-                const int W = 1 << (k - 5);
-                for (int e = lane; e < act * W; e += 32) {
-                    const int p = e / W, w = e % W;
-                    uint32_t* dst = cb + scl_coff(kc, L) + ptrC[kc * 32 + p] * scl_cw(kc);
-                    const uint32_t ck = cb[scl_coff(k, L) + ptrC[k * 32 + p] * scl_cw(k) + w];
-                    const uint32_t x = dst[w];
-                    dst[W + w] = x;
-                    dst[w] = x ^ ck;
+                const int W = 1 << (k - 5), total = act * W;
+                const uint32_t* ckb = S.Cl(k);
+                const uint32_t my_k = fld(pC, k);
+                for (int e0 = 0; e0 < total; e0 += 32) {
+                    const int e = e0 + lane;
+                    const int p = (e / W) & 31;
+                    const uint32_t pd = __shfl_sync(0xffffffffu, my_dst, p);
+                    const uint32_t pk = __shfl_sync(0xffffffffu, my_k, p);
+                    if (e < total) {
+                        const int w = e % W;
+                        uint32_t* dst = dstl + pd * cwk;
+                        const uint32_t x = dst[w];
+                        dst[W + w] = x;
+                        dst[w] = x ^ ckb[pk * scl_cw(k) + w];
+                    }
                 }
                 __syncwarp();
             }
@@ -256,9 +313,11 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
     // u = x G on each path's N-bit codeword (level-n array), in place; syndrome of its
     // information bits
     const int words = N >> 5;
+    uint32_t* xl = S.Cl(n);
+    const uint32_t my_x = fld(pC, n);
     uint32_t synd = 0xffffffffu;  // lane p: syndrome of path p
     for (int p = 0; p < act; ++p) {
-        uint32_t* xw = cb + scl_coff(n, L) + ptrC[n * 32 + p] * scl_cw(n);
+        uint32_t* xw = xl + __shfl_sync(0xffffffffu, my_x, p) * words;
         uint32_t w[2] = {0u, 0u};
 #pragma unroll
         for (int h = 0; h < 2; ++h)
@@ -309,7 +368,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             who = ow;
         }
     }
-    const uint32_t* uw = cb + scl_coff(n, L) + ptrC[n * 32 + who] * scl_cw(n);
+    const uint32_t* uw = xl + __shfl_sync(0xffffffffu, my_x, who & 31) * words;
     uint8_t* out = a.bits + (size_t)frame * a.row_bytes;
     for (int by = lane; by < a.row_bytes; by += 32) {
         uint32_t v = 0u;
@@ -325,22 +384,24 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(128) scl_kernel(const SCLArgs a, int llr_in_smem, int warp_words)
+template <bool TWO>
+__global__ void __launch_bounds__(kSclWarpsPerCTA * 32) scl_kernel(const SCLArgs a)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const DevCode& C = *a.code;
-    const int N = C.N, n = C.n, L = a.L;
-    uint32_t* cb = smem + (size_t)wid * warp_words;
-    uint8_t* ptrA = reinterpret_cast<uint8_t*>(cb + scl_coff(n + 1, L));
-    uint8_t* ptrC = ptrA + (n + 1) * 32;
-    uint8_t* selc = ptrC + (n + 1) * 32;
-    float* A;
-    if (llr_in_smem) {
-        A = reinterpret_cast<float*>(cb + ((scl_small_words(n, L) + 3) & ~3));
-    } else {
-        A = a.scratch + ((size_t)blockIdx.x * (blockDim.x >> 5) + wid) * (size_t)L * (N - 2);
-    }
+    const int L = a.L;
+    uint32_t* ws = smem + (size_t)wid * a.warp_words;
+    SCLWarp S;
+    S.L = L;
+    S.KS = a.KS;
+    S.KC = a.KC;
+    S.sC = ws;
+    S.sA = reinterpret_cast<float*>(ws + L * scl_cwsum(a.KC + 1));
+    uint8_t* selc = reinterpret_cast<uint8_t*>(ws + a.warp_words - 16);
+    float* slot = a.scratch ? a.scratch + ((size_t)blockIdx.x * (blockDim.x >> 5) + wid) * (size_t)a.slot_words : nullptr;
+    S.gA = slot;
+    S.gC = slot ? reinterpret_cast<uint32_t*>(slot + (size_t)L * (C.N - (2 << a.KS))) : nullptr;
     const int count = a.count ? *a.count : a.B;
     for (;;) {
         int idx = 0;
@@ -348,32 +409,42 @@ __global__ void __launch_bounds__(128) scl_kernel(const SCLArgs a, int llr_in_sm
         idx = __shfl_sync(0xffffffffu, idx, 0);
         if (idx >= count) break;
         const int frame = a.list ? a.list[idx] : idx;
-        scl_decode_frame(a, C, frame, cb, ptrA, ptrC, selc, A);
+        scl_decode_frame<TWO>(a, C, frame, S, selc);
     }
 }
 
-// Persistent launch: as many CTAs as fit on the device (bounded by the work when it is known on
-// the host); returns cudaSuccess or the launch error.
-inline cudaError_t scl_launch(const SCLArgs& a, int N, int L, cudaStream_t st)
+// Persistent launch: as many CTAs as fit on the device (bounded by the global slots and, when it
+// is known on the host, by the work); returns cudaSuccess or the launch error.  `a.scratch` null
+// selects the all-shared-memory layout.
+inline cudaError_t scl_launch(SCLArgs a, int N, int L, cudaStream_t st)
 {
-    const bool in_smem = scl_fits_smem(N, L);
-    const size_t wb = scl_warp_smem_bytes(N, L);
-    int W = 4;
+    const bool all_smem = a.scratch == nullptr;
+    const SCLPlan p = scl_plan(N, L, all_smem);
+    a.KS = p.KS;
+    a.KC = p.KC;
+    a.warp_words = p.warp_words;
+    a.slot_words = p.slot_words;
+    int W = kSclWarpsPerCTA;
+    const size_t wb = (size_t)p.warp_words * 4;
     while (W > 1 && (size_t)W * wb > 200 * 1024) W >>= 1;
     const size_t smem = (size_t)W * wb;
-    cudaError_t e = cudaFuncSetAttribute(scl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool two = L > 16;
+    const void* fn = two ? (const void*)scl_kernel<true> : (const void*)scl_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scl_kernel, W * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, W * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int sms = scl_sm_count();
     long long grid = (long long)sms * per_sm;
-    if (!in_smem) grid = std::min<long long>(grid, (long long)sms * kSclGlobalWarpsPerSM / W);
+    if (!all_smem) grid = std::min<long long>(grid, (long long)sms * kSclWarpsPerSM / W);
     if (!a.list) grid = std::min<long long>(grid, (a.B + W - 1) / W);
     if (grid < 1) grid = 1;
-    const int warp_words = (int)(wb / 4);
-    scl_kernel<<<(unsigned)grid, W * 32, smem, st>>>(a, in_smem ? 1 : 0, warp_words);
+    if (two)
+        scl_kernel<true><<<(unsigned)grid, W * 32, smem, st>>>(a);
+    else
+        scl_kernel<false><<<(unsigned)grid, W * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
