@@ -34,7 +34,7 @@ SEED = 1609093581
 def parse():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp16"], default="fp32")
@@ -60,9 +60,9 @@ def dist_setup():
 
 
 # ----------------------------------------------------------------------------- clocks
-QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
 class ClockSampler:
@@ -93,17 +93,29 @@ class ClockSampler:
         except Exception:
             pass
 
-    def summary(self):
+    def mark(self):
+        return time.time()
+
+    def summary(self, t0=None, t1=None):
+        """Samples taken between wall times t0 and t1 (the timed region)."""
+        import datetime
         rows = []
         try:
             for line in open(self.path):
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                if t0 is not None and not (t0 - 0.05 <= ts <= t1 + 0.05):
+                    continue
+                rows.append(parts[1:])
         except Exception:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock samples in the timed region"]}
 
         def num(v):
             try:
@@ -223,17 +235,24 @@ def main():
     n_fb = int(np.sum(status != api.FRAME_BP_OK))
 
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    api.polar_profile_enable(True)
     with ClockSampler(local) as clk:
+        time.sleep(1.0)  # let the sampler start; samples are filtered to the timed window
+        for _ in range(2):
+            step()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        api.polar_profile_enable(True)
+        t_start = clk.mark()
         e0.record(stream)
         for _ in range(a.steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
-    api.polar_profile_enable(False)
+        t_end = clk.mark()
+        api.polar_profile_enable(False)
+        time.sleep(0.3)
+    clocks = clk.summary(t_start, t_end)
     bp_ms, bp_n, scl_ms, scl_n = api.polar_profile_read()
     ms = e0.elapsed_time(e1)
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -256,7 +275,9 @@ def main():
     lanes = 128 * (2 if prec == api.POLAR_FP16 else 1)
     peak_ops = sms * lanes * sm_max_mhz * 1e6
     bp_avg_ms = bp_ms / max(bp_n, 1)
-    achieved = ops_per_frame_iter * float(iters.sum()) / (bp_avg_ms * 1e-3)
+    # every step decodes the same frames: total algorithmic ops of the timed BP launches over their
+    # summed device time (= ops per launch / average launch time when a step is one launch)
+    achieved = ops_per_frame_iter * float(iters.sum()) * a.steps / (bp_ms * 1e-3)
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if os.path.exists(tfile):
@@ -278,7 +299,7 @@ def main():
                        "cache": "inputs larger than L2 (%.0f MB of LLRs per step per GPU), no flush" % (B * N * 4 / 1e6)},
             "fer": fer, "ber": bit_err / (B * P), "fallback_rate": n_fb / B, "avg_bp_iters": float(iters.mean()),
             "bp_ms_per_step": bp_ms / a.steps, "scl_ms_per_step": scl_ms / a.steps,
-            "gpu_launches": bp_n + scl_n, "roofline": roofline, "clocks": clk.summary()}
+            "gpu_launches": bp_n + scl_n, "roofline": roofline, "clocks": clocks}
 
     if not a.no_e2e:
         line["e2e"] = e2e(a, code, llr, prec, llr_max, dev, stream, dist)

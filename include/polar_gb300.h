@@ -94,11 +94,13 @@ int polar_encode(const polar_code* code, const uint8_t* payload, int32_t B, uint
  * frame0 + b.  polar_random_payload: stream 0, bit p of a frame is bit p % 32 of word p / 32.
  * polar_awgn_llr: stream 1, Box-Muller on 24-bit uniforms; llr = 2 (1 - 2x + sigma z) / sigma^2
  * (the LLR definition of Sec. II-A).  payload: device [B][ceil(P/8)]; codeword: device [B][N/8]
- * packed; llr: device float [B][N]. */
+ * packed; llr: device float [B][N]; sigma_per_frame: NULL (every frame uses sigma) or device
+ * float [B]. */
 int polar_random_payload(int32_t B, int32_t P, uint64_t seed, uint64_t frame0, uint8_t* payload,
                          void* stream);
-int polar_awgn_llr(const uint8_t* codeword, int32_t B, int32_t N, float sigma, uint64_t seed,
-                   uint64_t frame0, float* llr, void* stream);
+int polar_awgn_llr(const uint8_t* codeword, int32_t B, int32_t N, float sigma,
+                   const float* sigma_per_frame, uint64_t seed, uint64_t frame0, float* llr,
+                   void* stream);
 
 /* Min-sum belief propagation with CRC early stop (Sec. II-B; PE of Fig. 2 on the graph of
  * Fig. 1).  One iteration updates the R messages of columns 2..n+1, then the L messages of
@@ -144,6 +146,21 @@ int hybrid_decode(const polar_code* code, const float* llr, int32_t B, int32_t m
                   float llr_max, int32_t precision, const float* wms_scales, int32_t wms_iters,
                   int32_t L, uint8_t* bits, uint8_t* status, uint16_t* iters, void* workspace,
                   size_t ws_bytes, void* stream);
+
+/* Training of the learned weighted min-sum BP (the configurations' learned variant; not in the
+ * paper).  wms_forward runs T iterations of the weighted BP of bp_decode (no early stop) and
+ * writes LLR(u) = L_{.,1} + R_{.,1} of the last iteration, storing every message in the
+ * workspace; wms_backward, given dLoss/dLLR(u), writes dLoss/dw for w[T][2][n][N] (overwritten,
+ * summed over the batch) by a hand-written reverse sweep through the stored messages
+ * (subgradients of min and clip).  Call wms_backward after wms_forward with the same llr, w and
+ * workspace.  llr, w, llr_u, grad_llr_u, grad_w: device.  workspace: device, >=
+ * wms_workspace_bytes(code, B, T).  1 <= T <= 1000. */
+size_t wms_workspace_bytes(const polar_code* code, int32_t B, int32_t T);
+int wms_forward(const polar_code* code, const float* llr, int32_t B, int32_t T, float llr_max,
+                const float* w, float* llr_u, void* workspace, size_t ws_bytes, void* stream);
+int wms_backward(const polar_code* code, const float* llr, int32_t B, int32_t T, float llr_max,
+                 const float* w, const float* grad_llr_u, float* grad_w, void* workspace,
+                 size_t ws_bytes, void* stream);
 
 /* hybrid_decode on frames that live in host memory (not a step of the paper; its Sec. III
  * rejects moving SCL to the CPU because of transfer latency, which is what this hides).  The

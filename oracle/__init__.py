@@ -83,8 +83,9 @@ def _declare(L):
     for sfx in ("f32", "f64", "f16"):
         getattr(L, "or_bp_decode_batch_" + sfx).argtypes = [
             _f32p, _c_int, _c_int, _u8p, _i32p, _c_int, _c_uint, _c_int, _c_int, _c_double, _c_int,
-            _f32p, _c_int, _u8p, _u8p, _i32p, _f32p, _f32p]
+            _f32p, _c_int, _u8p, _u8p, _i32p, _f32p, _f32p, _f64p]
     for sfx in ("f32", "f64"):
+        getattr(L, "or_wms_grad_" + sfx).argtypes = [_f32p, _c_int, _u8p, _c_int, _c_double, _f32p, _f64p, _f64p]
         getattr(L, "or_sc_decode_" + sfx).argtypes = [_f32p, _c_int, _u8p, _u8p]
         getattr(L, "or_sc_bit_llr_" + sfx).argtypes = [_f32p, _c_int, _u8p, _c_int]
         getattr(L, "or_sc_bit_llr_" + sfx).restype = _c_double
@@ -240,7 +241,7 @@ def round_half(x: float) -> float:
 
 # ---------------------------------------------------------------- decoders
 def bp_decode(llr, code: Code, max_iters: int, llr_max: float, precision: str = "f32",
-              early_stop: bool = True, w=None, want_llr: bool = True) -> dict:
+              early_stop: bool = True, w=None, want_llr: bool = True, llr_u_double: bool = False) -> dict:
     """Min-sum BP with CRC early stop on a batch llr float32 [B][N] (Sec. II-B)."""
     llr = _f32(llr).reshape(-1, code.N)
     B, N = llr.shape
@@ -249,6 +250,7 @@ def bp_decode(llr, code: Code, max_iters: int, llr_max: float, precision: str = 
     it = np.zeros(B, np.int32)
     lu = np.zeros((B, N), np.float32) if want_llr else None
     lx = np.zeros((B, N), np.float32) if want_llr else None
+    lud = np.zeros((B, N), np.float64) if llr_u_double else None
     w_iters = 0
     if w is not None:
         w = _f32(w)
@@ -257,8 +259,22 @@ def bp_decode(llr, code: Code, max_iters: int, llr_max: float, precision: str = 
     getattr(lib(), "or_bp_decode_batch_" + precision)(
         _p(llr, _f32p), B, N, _p(code.frozen, _u8p), _p(code.info_idx, _i32p), code.K,
         code.crc_poly, code.crc_len, max_iters, llr_max, int(early_stop), _p(w, _f32p), w_iters,
-        _p(u, _u8p), _p(st, _u8p), _p(it, _i32p), _p(lu, _f32p), _p(lx, _f32p))
-    return {"u_hat": u, "status": st, "iters": it, "llr_u": lu, "llr_x": lx}
+        _p(u, _u8p), _p(st, _u8p), _p(it, _i32p), _p(lu, _f32p), _p(lx, _f32p), _p(lud, _f64p))
+    return {"u_hat": u, "status": st, "iters": it, "llr_u": lu, "llr_x": lx, "llr_u_f64": lud}
+
+
+def wms_grad(llr, code: Code, T: int, llr_max: float, w, dy, precision: str = "f64") -> np.ndarray:
+    """d/dw of sum_b sum_i dy[b][i] LLR(u_i) after T weighted BP iterations (no early stop)."""
+    llr = _f32(llr).reshape(-1, code.N)
+    dy = np.ascontiguousarray(dy, dtype=np.float64).reshape(llr.shape)
+    w = _f32(w)
+    g = np.zeros(w.shape, np.float64)
+    fn = getattr(lib(), "or_wms_grad_" + precision)
+    for b in range(llr.shape[0]):
+        row = np.ascontiguousarray(llr[b])
+        fn(_p(row, _f32p), code.N, _p(code.frozen, _u8p), T, llr_max, _p(w, _f32p), _p(np.ascontiguousarray(dy[b]), _f64p),
+           _p(g, _f64p))
+    return g
 
 
 def sc_decode(llr, code: Code, precision: str = "f32") -> np.ndarray:

@@ -42,7 +42,10 @@ SIGNATURES = {
     "polar_construct": (ctypes.c_int, [_i32, _i32, _f64, _f64, _vp, _vp]),
     "polar_encode": (ctypes.c_int, [_CP, _vp, _i32, _vp, _vp]),
     "polar_random_payload": (ctypes.c_int, [_i32, _i32, _u64, _u64, _vp, _vp]),
-    "polar_awgn_llr": (ctypes.c_int, [_vp, _i32, _i32, _f32, _u64, _u64, _vp, _vp]),
+    "polar_awgn_llr": (ctypes.c_int, [_vp, _i32, _i32, _f32, _vp, _u64, _u64, _vp, _vp]),
+    "wms_workspace_bytes": (_sz, [_CP, _i32, _i32]),
+    "wms_forward": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _vp, _vp, _vp, _sz, _vp]),
+    "wms_backward": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _vp, _vp, _vp, _vp, _sz, _vp]),
     "bp_decode": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
                                  _vp]),
     "scl_decode": (ctypes.c_int, [_CP, _vp, _i32, _i32, _vp, _vp, _vp, _sz, _vp]),
@@ -160,10 +163,30 @@ def polar_random_payload(B: int, P: int, seed: int, frame0: int, payload, stream
            "polar_random_payload")
 
 
-def polar_awgn_llr(codeword, N: int, sigma: float, seed: int, frame0: int, llr, stream=None) -> None:
+def polar_awgn_llr(codeword, N: int, sigma: float, seed: int, frame0: int, llr, stream=None,
+                   sigma_per_frame=None) -> None:
     B = codeword.shape[0]
-    _check(load().polar_awgn_llr(_ptr(codeword), B, N, sigma, seed, frame0, _ptr(llr), _stream(stream)),
-           "polar_awgn_llr")
+    _check(load().polar_awgn_llr(_ptr(codeword), B, N, sigma, _ptr(sigma_per_frame), seed, frame0, _ptr(llr),
+                                 _stream(stream)), "polar_awgn_llr")
+
+
+def wms_workspace_bytes(code: PolarCode, B: int, T: int) -> int:
+    return int(load().wms_workspace_bytes(code.ref(), B, T))
+
+
+def wms_forward(code: PolarCode, llr, T: int, llr_max: float, w, llr_u, workspace, stream=None) -> None:
+    B = llr.shape[0]
+    ws_b = workspace.numel() * workspace.element_size()
+    _check(load().wms_forward(code.ref(), _ptr(llr), B, T, llr_max, _ptr(w), _ptr(llr_u), _ptr(workspace), ws_b,
+                              _stream(stream)), "wms_forward")
+
+
+def wms_backward(code: PolarCode, llr, T: int, llr_max: float, w, grad_llr_u, grad_w, workspace,
+                 stream=None) -> None:
+    B = llr.shape[0]
+    ws_b = workspace.numel() * workspace.element_size()
+    _check(load().wms_backward(code.ref(), _ptr(llr), B, T, llr_max, _ptr(w), _ptr(grad_llr_u), _ptr(grad_w),
+                               _ptr(workspace), ws_b, _stream(stream)), "wms_backward")
 
 
 def polar_workspace_bytes(code: PolarCode, B: int, L: int, op: int) -> int:

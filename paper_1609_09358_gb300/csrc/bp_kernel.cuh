@@ -32,24 +32,6 @@
 
 namespace polar {
 
-template <int I, int E, class Fn>
-__device__ __forceinline__ void static_for(Fn&& fn)
-{
-    if constexpr (I < E) {
-        fn(std::integral_constant<int, I>{});
-        static_for<I + 1, E>(fn);
-    }
-}
-
-template <int I, int E, class Fn>  // I, I-1, ..., E
-__device__ __forceinline__ void static_for_down(Fn&& fn)
-{
-    if constexpr (I >= E) {
-        fn(std::integral_constant<int, I>{});
-        static_for_down<I - 1, E>(fn);
-    }
-}
-
 template <int LOGN_, int LOGR_>
 struct BPPlan {
     static constexpr int LOGN = LOGN_, LOGR = LOGR_;
@@ -132,6 +114,8 @@ struct BPArgs {
     const DevCode* code;
     int* fail_count;  // hybrid: compaction of the CRC-failed frames (null for bp_decode)
     int* fail_list;
+    int* fail_total;  // optional running total of CRC-failed frames
+    int* next;        // work counter (zero before the launch): groups refill from it; null = one frame group per CTA slot
     int row_bytes;
 };
 
@@ -148,6 +132,9 @@ struct MsgTraits<float> {
     }
     __device__ static bool neg(float v, int h) { return v < 0.0f; }
     __device__ static float to_f(float v, int h) { return v; }
+    __device__ static float set_half(float, float x, int) { return x; }
+    __device__ static float zero_half(float, int) { return 0.0f; }
+    __device__ static float pair(float a, float) { return a; }
 };
 template <>
 struct MsgTraits<__half2> {
@@ -164,6 +151,17 @@ struct MsgTraits<__half2> {
         return __hlt(h ? __high2half(v) : __low2half(v), __float2half(0.0f));
     }
     __device__ static float to_f(__half2 v, int h) { return __half2float(h ? __high2half(v) : __low2half(v)); }
+    __device__ static __half2 set_half(__half2 v, float x, int h)
+    {
+        const __half hx = __float2half_rn(x);
+        return h ? __halves2half2(__low2half(v), hx) : __halves2half2(hx, __high2half(v));
+    }
+    __device__ static __half2 zero_half(__half2 v, int h)
+    {
+        const __half z = __float2half_rn(0.0f);
+        return h ? __halves2half2(__low2half(v), z) : __halves2half2(z, __high2half(v));
+    }
+    __device__ static __half2 pair(float a, float b) { return __floats2half2_rn(a, b); }
 };
 
 template <int LOGN>
@@ -178,8 +176,8 @@ template <class P>
 __host__ __device__ constexpr int bp_slot_words()
 {
     // exchange buffer [2][N] | syndrome columns, thread-major [R][T] | partial syndromes
-    // [2][2][NW] | packed payload bits [2][N/32]
-    return 2 * P::N + P::N + 4 * P::NW + 2 * (P::N / 32);
+    // [2][2][NW] | packed payload bits [2][N/32] | fetched frame index [4]
+    return 2 * P::N + P::N + 4 * P::NW + 2 * (P::N / 32) + 4;
 }
 
 // THREADS = F * T (passed explicitly: launch bounds take no dependent member expression)
@@ -203,14 +201,32 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
     extern __shared__ uint32_t smem[];
     const int slot = threadIdx.x / T;
     const int t = threadIdx.x % T;
-    const int frame0 = (blockIdx.x * F + slot) * FPT;  // first frame of this thread group
-    if (frame0 >= a.B) return;  // whole frame groups leave together
-    const bool has1 = FPT == 2 && frame0 + 1 < a.B;
-
     MSG* xbuf = reinterpret_cast<MSG*>(smem + slot * SW);  // [2][N]; half2 uses the first half
     uint32_t* csyn = smem + slot * SW + 2 * N;             // [R][T]
     uint32_t* synp = csyn + N;                             // [2 parity][2 frame][NW]
     uint32_t* pbits = synp + 4 * NW;                       // [2 frame][N/32]
+    int* fetched = reinterpret_cast<int*>(pbits + 2 * (N / 32));
+
+    // Frames of this group: half h (h < FPT) decodes frame fr[h]; when it stops it fetches the
+    // next frame from the work counter (or, without one, the group's single static frame group).
+    int nfetch = 0;
+    auto fetch = [&]() -> int {
+        int f;
+        if (a.next) {
+            if (t == 0) fetched[0] = atomicAdd(a.next, 1);
+            frame_sync<T>(slot);
+            f = fetched[0];
+            frame_sync<T>(slot);
+        } else {
+            f = nfetch < FPT ? (blockIdx.x * F + slot) * FPT + nfetch : a.B;
+        }
+        ++nfetch;
+        return f < a.B ? f : -1;
+    };
+    int fr[2] = {-1, -1}, itc[2] = {0, 0};
+    fr[0] = fetch();
+    if constexpr (FPT == 2) fr[1] = fetch();
+    if (fr[0] < 0 && fr[1] < 0) return;  // uniform over the group
     const DevCode& C = *a.code;
     const float M = a.llr_max;
     const MSG Mv = MT::splat(M);
@@ -224,10 +240,13 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
         Rc[1][k] = frozen_at(C.frozen_bits, j) ? Mv : MT::splat(0.0f);
     }
     {
-        const float* y0 = a.llr + (size_t)frame0 * N;
-        const float* y1 = has1 ? y0 + N : nullptr;
+        const float* y0 = fr[0] >= 0 ? a.llr + (size_t)fr[0] * N : nullptr;
+        const float* y1 = fr[1] >= 0 ? a.llr + (size_t)fr[1] * N : nullptr;
 #pragma unroll
-        for (int k = 0; k < R; ++k) Lc[n + 1][k] = MT::load2(y0, y1, P::node(NG - 1, t, k), M);
+        for (int k = 0; k < R; ++k) {
+            const int j = P::node(NG - 1, t, k);
+            Lc[n + 1][k] = MT::pair(y0 ? stage_clip(__ldg(y0 + j), M) : 0.0f, y1 ? stage_clip(__ldg(y1 + j), M) : 0.0f);
+        }
     }
 #pragma unroll
     for (int c = 2; c <= n; ++c)
@@ -237,14 +256,22 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
             Rc[c][k] = MT::splat(0.0f);
         }
 
-    auto weight = [&](int it, int dir, int s, int j) -> MSG {
-        return MT::splat(__ldg(a.w + (((size_t)it * 2 + dir) * n + (s - 1)) * N + j));
+    // learned scale of iteration `it` (1 past the learned iterations: the same value as the plain
+    // update, since 1 * g = g and |g| <= M needs no clip)
+    auto wval = [&](int it, int dir, int s, int j) -> float {
+        return it < a.w_iters ? __ldg(a.w + (((size_t)it * 2 + dir) * n + (s - 1)) * N + j) : 1.0f;
+    };
+    auto weight = [&](int dir, int s, int j) -> MSG {
+        if constexpr (FPT == 2)
+            return MT::pair(wval(itc[0], dir, s, j), wval(itc[1], dir, s, j));
+        else
+            return MT::splat(wval(itc[0], dir, s, j));
     };
 
     // write the decided payload bits, status and optional LLRs of frame half h after `it_done`
     // iterations; called uniformly by the T threads of the frame group
     auto finalize = [&](int h, int it_done, bool ok) {
-        const int frame = frame0 + h;
+        const int frame = fr[h];
         uint32_t* pb = pbits + h * (N / 32);
         for (int i = t; i < N / 32; i += T) pb[i] = 0u;
         frame_sync<T>(slot);
@@ -261,7 +288,10 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
         if (t == 0) {
             a.iters[frame] = (uint16_t)it_done;
             a.status[frame] = ok ? POLAR_FRAME_BP_OK : POLAR_FRAME_BP_FAIL;
-            if (!ok && a.fail_list) a.fail_list[atomicAdd(a.fail_count, 1)] = frame;
+            if (!ok && a.fail_list) {
+                a.fail_list[atomicAdd(a.fail_count, 1)] = frame;
+                if (a.fail_total) atomicAdd(a.fail_total, 1);
+            }
         }
         if (a.llr_u) {
 #pragma unroll
@@ -278,10 +308,11 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
                 MSG o1 = xmin(Rc[n][k], fadd(Lc[n + 1][k2], Rc[n][k2]));
                 MSG gg = xmin(Rc[n][k], Lc[n + 1][k]);
                 if constexpr (WEIGHTED) {
-                    if (it_done - 1 < a.w_iters) {
-                        o1 = clipm(fmul(weight(it_done - 1, 0, n, P::node(g, t, k)), o1), Mv);
-                        gg = fmul(weight(it_done - 1, 0, n, P::node(g, t, k2)), gg);
-                    }
+                    // itc of this half was already advanced past the last iteration
+                    const MSG w1 = MT::splat(wval(it_done - 1, 0, n, P::node(g, t, k)));
+                    const MSG w2 = MT::splat(wval(it_done - 1, 0, n, P::node(g, t, k2)));
+                    o1 = clipm(fmul(w1, o1), Mv);
+                    gg = fmul(w2, gg);
                 }
                 const MSG o2 = clipm(fadd(gg, Rc[n][k2]), Mv);
                 a.llr_x[(size_t)frame * N + P::node(g, t, k)] = MT::to_f(fadd(Lc[n + 1][k], o1), h);
@@ -290,10 +321,27 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
         }
     };
 
-    bool done0 = false, done1 = !has1 && FPT == 2;
-    int it = 0;
-    while (it < a.max_iters) {
-        const bool wt = WEIGHTED && it < a.w_iters;
+    // replace the frame of half h by the next one: channel column and zeroed messages
+    auto refill = [&](int h) {
+        fr[h] = fetch();
+        itc[h] = 0;
+        const float* y = fr[h] >= 0 ? a.llr + (size_t)fr[h] * N : nullptr;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const float v = y ? stage_clip(__ldg(y + P::node(NG - 1, t, k)), M) : 0.0f;
+            Lc[n + 1][k] = MT::set_half(Lc[n + 1][k], v, h);
+        }
+#pragma unroll
+        for (int c = 2; c <= n; ++c)
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                Lc[c][k] = MT::zero_half(Lc[c][k], h);
+                Rc[c][k] = MT::zero_half(Rc[c][k], h);
+            }
+    };
+
+    int it = 0;  // iterations run by this group (selects the partial-syndrome slot parity)
+    for (;;) {
         // ------------------------------------------------------------------ R sweep
         static_for<1, n + 1>([&](auto S) {
             constexpr int s = S.value, q = s - 1, g = P::grp(q), dd = 1 << (q - P::win(g));
@@ -308,10 +356,8 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
                 MSG o1 = xmin(a1, fadd(l2, a2));
                 MSG gg = xmin(a1, l1);
                 if constexpr (WEIGHTED) {
-                    if (wt) {
-                        o1 = clipm(fmul(weight(it, 0, s, P::node(g, t, k)), o1), Mv);
-                        gg = fmul(weight(it, 0, s, P::node(g, t, k2)), gg);
-                    }
+                    o1 = clipm(fmul(weight(0, s, P::node(g, t, k)), o1), Mv);
+                    gg = fmul(weight(0, s, P::node(g, t, k2)), gg);
                 }
                 const MSG o2 = clipm(fadd(gg, a2), Mv);
                 if constexpr (!last) {
@@ -345,10 +391,8 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
                 MSG o1 = xmin(l1, fadd(l2, a2));
                 MSG gg = xmin(a1, l1);
                 if constexpr (WEIGHTED) {
-                    if (wt) {
-                        o1 = clipm(fmul(weight(it, 1, s, P::node(g, t, k)), o1), Mv);
-                        gg = fmul(weight(it, 1, s, P::node(g, t, k2)), gg);
-                    }
+                    o1 = clipm(fmul(weight(1, s, P::node(g, t, k)), o1), Mv);
+                    gg = fmul(weight(1, s, P::node(g, t, k2)), gg);
                 }
                 const MSG o2 = clipm(fadd(gg, l2), Mv);
                 if constexpr (cross) {
@@ -395,23 +439,20 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
             }
         }
         ++it;
-        if (!done0 && syn0 == 0) {
-            done0 = true;
-            finalize(0, it, true);
-        }
-        if constexpr (FPT == 2) {
-            if (!done1 && syn1 == 0) {
-                done1 = true;
-                finalize(1, it, true);
+        const uint32_t syn[2] = {syn0, syn1};
+        bool any = false;
+#pragma unroll
+        for (int h = 0; h < FPT; ++h) {
+            if (fr[h] < 0) continue;
+            ++itc[h];
+            const bool ok = syn[h] == 0u;
+            if (ok || itc[h] >= a.max_iters) {
+                finalize(h, itc[h], ok);
+                refill(h);
             }
-            if (done0 && done1) break;
-        } else {
-            if (done0) break;
+            any |= fr[h] >= 0;
         }
-    }
-    if (!done0) finalize(0, it, false);
-    if constexpr (FPT == 2) {
-        if (!done1) finalize(1, it, false);
+        if (!any) break;
     }
 }
 

@@ -115,13 +115,15 @@ __global__ void random_payload_kernel(int B, int P, uint64_t seed, uint64_t fram
 }
 
 // One thread per Philox block (4 nodes) of one frame: Box-Muller on (w0, w1) and (w2, w3).
-__global__ void awgn_llr_kernel(const uint8_t* __restrict__ codeword, int B, int N, float sigma,
-                                uint64_t seed, uint64_t frame0, float* __restrict__ llr)
+__global__ void awgn_llr_kernel(const uint8_t* __restrict__ codeword, int B, int N, float sigma_all,
+                                const float* __restrict__ sigmas, uint64_t seed, uint64_t frame0,
+                                float* __restrict__ llr)
 {
     const int nblocks = N >> 2;
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)B * nblocks) return;
     const int b = (int)(gid / nblocks), blk = (int)(gid % nblocks);
+    const float sigma = sigmas ? sigmas[b] : sigma_all;
     const uint64_t f = frame0 + (uint64_t)b;
     const U4 r = philox4x32_10(U4{(uint32_t)blk, (uint32_t)f, 1u, (uint32_t)(f >> 32)}, (uint32_t)seed,
                                (uint32_t)(seed >> 32));

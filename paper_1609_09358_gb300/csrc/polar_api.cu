@@ -14,6 +14,7 @@
 #include "encode_kernels.cuh"
 #include "polar_common.cuh"
 #include "scl_kernel.cuh"
+#include "wms_kernels.cuh"
 
 namespace polar {
 
@@ -168,6 +169,18 @@ static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 static size_t ws_bytes(const polar_code* code, int B, int L, int op);
 
+// hybrid_decode: one BP launch over the batch, then one persistent CA-SCL launch over the
+// frames it compacted.  (Cutting the batch into chunks whose CA-SCL overlaps later BP chunks was
+// measured slower: each CA-SCL launch costs at least one frame's decoding latency, and the frames
+// BP fails are the ones that run all i_max iterations, i.e. the last to leave BP.)
+struct ChunkHdr {
+    int fail_count;
+    int scl_next;
+    int bp_next;
+    int pad;
+};
+static size_t hybrid_chunk_header_bytes(int) { return 256; }
+
 // One chunk's device buffers of hybrid_decode_host: LLRs, bits, status, iterations, hybrid
 // workspace; two such sets alternate.
 struct HostSet {
@@ -201,7 +214,10 @@ static size_t ws_bytes(const polar_code* code, int B, int L, int op)
         return 2 * host_set_layout(code, chunk, L).total;
     }
     size_t b = kHeaderBytes;
-    if (op == POLAR_OP_HYBRID) b += align_up(sizeof(int) * (size_t)std::max(B, 1), 256);
+    if (op == POLAR_OP_HYBRID) {
+        b += hybrid_chunk_header_bytes(B);
+        b += align_up(sizeof(int) * (size_t)std::max(B, 1), 256);
+    }
     b += scl_scratch_bytes(code->N, L);
     return b;
 }
@@ -219,6 +235,8 @@ static int aux_stream(cudaStream_t* out)
     *out = g_aux[dev];
     return POLAR_OK;
 }
+
+
 
 // ---------------------------------------------------------------------------- kernel timing
 struct ProfRecord {
@@ -269,9 +287,11 @@ struct ProfScope {
 static int launch_bp(const DevCode* dcode, const polar_code* code, const float* llr, int B, int max_iters,
                      float llr_max, int precision, const float* w, int w_iters, uint8_t* bits, uint8_t* status,
                      uint16_t* iters, float* llr_u, float* llr_x, int* fail_count, int* fail_list,
-                     cudaStream_t stream)
+                     cudaStream_t stream, int* fail_total = nullptr, int* next = nullptr)
 {
     BPArgs a{};
+    a.fail_total = fail_total;
+    a.next = next;
     a.llr = llr;
     a.B = B;
     a.max_iters = max_iters;
@@ -294,18 +314,21 @@ static int launch_bp(const DevCode* dcode, const polar_code* code, const float* 
         using P = typename Cfg::Plan;
         const int fpt = precision == POLAR_FP16 ? 2 : 1;
         const int groups = (B + fpt - 1) / fpt;
-        const int grid = (groups + Cfg::F - 1) / Cfg::F;
+        int grid = (groups + Cfg::F - 1) / Cfg::F;
         const size_t smem = (size_t)Cfg::F * bp_slot_words<P>() * 4;
-        const int threads = Cfg::F * P::T;
         constexpr int TH = Cfg::F * P::T;
-        if (precision == POLAR_FP16) {
-            if (w) bp_kernel<LOGN, __half2, true, TH><<<grid, threads, smem, stream>>>(a);
-            else bp_kernel<LOGN, __half2, false, TH><<<grid, threads, smem, stream>>>(a);
-        } else {
-            if (w) bp_kernel<LOGN, float, true, TH><<<grid, threads, smem, stream>>>(a);
-            else bp_kernel<LOGN, float, false, TH><<<grid, threads, smem, stream>>>(a);
+        const void* fn = precision == POLAR_FP16
+                             ? (w ? (const void*)bp_kernel<LOGN, __half2, true, TH> : (const void*)bp_kernel<LOGN, __half2, false, TH>)
+                             : (w ? (const void*)bp_kernel<LOGN, float, true, TH> : (const void*)bp_kernel<LOGN, float, false, TH>);
+        if (next) {
+            // persistent: as many CTAs as are resident at once; groups refill from the counter
+            int per_sm = 0, sms = scl_sm_count();
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TH, smem);
+            if (e != cudaSuccess) return cuda_fail(e, "bp occupancy");
+            grid = std::min(grid, std::max(1, per_sm) * sms);
         }
-        cudaError_t e = cudaGetLastError();
+        void* args[] = {&a};
+        cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(TH), args, smem, stream);
         return e == cudaSuccess ? POLAR_OK : cuda_fail(e, "bp_kernel launch");
     };
     if (B == 0) return POLAR_OK;
@@ -447,15 +470,16 @@ int polar_random_payload(int32_t B, int32_t P, uint64_t seed, uint64_t frame0, u
     return POLAR_OK;
 }
 
-int polar_awgn_llr(const uint8_t* codeword, int32_t B, int32_t N, float sigma, uint64_t seed, uint64_t frame0,
-                   float* llr, void* stream)
+int polar_awgn_llr(const uint8_t* codeword, int32_t B, int32_t N, float sigma, const float* sigma_per_frame,
+                   uint64_t seed, uint64_t frame0, float* llr, void* stream)
 {
-    if (B < 0 || !is_pow2(N) || N < 8 || !(sigma > 0.0f)) return fail(POLAR_ERR_ARG, "bad B, N or sigma");
+    if (B < 0 || !is_pow2(N) || N < 8 || (!sigma_per_frame && !(sigma > 0.0f)))
+        return fail(POLAR_ERR_ARG, "bad B, N or sigma");
     if (B == 0) return POLAR_OK;
     if (!codeword || !llr) return fail(POLAR_ERR_ARG, "NULL codeword/llr");
     const long long total = (long long)B * (N / 4);
     awgn_llr_kernel<<<(unsigned)((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        codeword, B, N, sigma, seed, frame0, llr);
+        codeword, B, N, sigma, sigma_per_frame, seed, frame0, llr);
     POLAR_CUDA(cudaGetLastError());
     return POLAR_OK;
 }
@@ -517,15 +541,17 @@ int hybrid_decode(const polar_code* code, const float* llr, int32_t B, int32_t m
     if (B == 0) return POLAR_OK;
     const size_t need = ws_bytes(code, B, L, POLAR_OP_HYBRID);
     if (!workspace || ws < need) return fail(POLAR_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws, need);
+    // [total fail count (256 B)][counters (256 B)][fail list][SCL scratch]
     char* base = static_cast<char*>(workspace);
-    WsHeader* h = reinterpret_cast<WsHeader*>(base);
-    int* list = reinterpret_cast<int*>(base + kHeaderBytes);
-    void* scratch = base + kHeaderBytes + align_up(sizeof(int) * (size_t)B, 256);
-    POLAR_CUDA(cudaMemsetAsync(h, 0, sizeof(WsHeader), st));
+    int* total = reinterpret_cast<int*>(base);
+    ChunkHdr* hdr = reinterpret_cast<ChunkHdr*>(base + kHeaderBytes);
+    int* list = reinterpret_cast<int*>(base + kHeaderBytes + hybrid_chunk_header_bytes(B));
+    void* scratch = reinterpret_cast<char*>(list) + align_up(sizeof(int) * (size_t)B, 256);
+    POLAR_CUDA(cudaMemsetAsync(base, 0, kHeaderBytes + sizeof(ChunkHdr), st));
     if ((rc = launch_bp(d, code, llr, B, max_iters, llr_max, precision, wms_scales, wms_iters, bits, status, iters,
-                        nullptr, nullptr, &h->fail_count, list, st)))
+                        nullptr, nullptr, &hdr->fail_count, list, st, total, &hdr->bp_next)))
         return rc;
-    return launch_scl(d, code, llr, B, L, bits, status, list, &h->fail_count, &h->scl_next, scratch, st);
+    return launch_scl(d, code, llr, B, L, bits, status, list, &hdr->fail_count, &hdr->scl_next, scratch, st);
 }
 
 int hybrid_decode_host(const polar_code* code, const float* llr_host, int32_t B, int32_t max_iters, float llr_max,
@@ -577,6 +603,72 @@ int hybrid_decode_host(const polar_code* code, const float* llr_host, int32_t B,
     cudaEventDestroy(ev_in);
     cudaEventDestroy(ev_out);
     return rc;
+}
+
+size_t wms_workspace_bytes(const polar_code* code, int32_t B, int32_t T)
+{
+    if (check_code(code) != POLAR_OK || B < 0 || T < 1) return 0;
+    const size_t n = (size_t)log2i(code->N), N = (size_t)code->N;
+    return (size_t)B * (2 * (size_t)T * n * N + 3 * (n + 2) * N) * sizeof(float);
+}
+
+static int wms_common(const polar_code* code, const float* llr, int B, int T, float llr_max, const float* w,
+                      void* workspace, size_t ws, cudaStream_t st, WMSArgs& a)
+{
+    int rc = check_code(code);
+    if (rc) return rc;
+    if (B < 0 || T < 1 || T > 1000) return fail(POLAR_ERR_ARG, "B = %d, T = %d", B, T);
+    if (!(llr_max > 0.0f)) return fail(POLAR_ERR_ARG, "llr_max must be > 0");
+    if (B > 0 && (!llr || !w)) return fail(POLAR_ERR_ARG, "NULL llr/w");
+    const size_t need = wms_workspace_bytes(code, B, T);
+    if (B > 0 && (!workspace || ws < need)) return fail(POLAR_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws, need);
+    const DevCode* d = nullptr;
+    if ((rc = code_slot(code, st, &d))) return rc;
+    const size_t n = (size_t)log2i(code->N), N = (size_t)code->N;
+    a = WMSArgs{};
+    a.llr = llr;
+    a.B = B;
+    a.T = T;
+    a.M = llr_max;
+    a.w = w;
+    a.store = static_cast<float*>(workspace);
+    a.adj = a.store + (size_t)B * 2 * T * n * N;
+    a.code = d;
+    return POLAR_OK;
+}
+
+int wms_forward(const polar_code* code, const float* llr, int32_t B, int32_t T, float llr_max, const float* w,
+                float* llr_u, void* workspace, size_t ws, void* stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    WMSArgs a;
+    int rc = wms_common(code, llr, B, T, llr_max, w, workspace, ws, st, a);
+    if (rc) return rc;
+    if (B == 0) return POLAR_OK;
+    if (!llr_u) return fail(POLAR_ERR_ARG, "NULL llr_u");
+    a.llr_u = llr_u;
+    wms_forward_kernel<<<B, code->N / 2, 0, st>>>(a);
+    POLAR_CUDA(cudaGetLastError());
+    return POLAR_OK;
+}
+
+int wms_backward(const polar_code* code, const float* llr, int32_t B, int32_t T, float llr_max, const float* w,
+                 const float* grad_llr_u, float* grad_w, void* workspace, size_t ws, void* stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    WMSArgs a;
+    int rc = wms_common(code, llr, B, T, llr_max, w, workspace, ws, st, a);
+    if (rc) return rc;
+    if (!grad_w) return fail(POLAR_ERR_ARG, "NULL grad_w");
+    const size_t n = (size_t)log2i(code->N), N = (size_t)code->N;
+    POLAR_CUDA(cudaMemsetAsync(grad_w, 0, (size_t)T * 2 * n * N * sizeof(float), st));
+    if (B == 0) return POLAR_OK;
+    if (!grad_llr_u) return fail(POLAR_ERR_ARG, "NULL grad_llr_u");
+    a.grad_u = grad_llr_u;
+    a.grad_w = grad_w;
+    wms_backward_kernel<<<B, code->N / 2, 0, st>>>(a);
+    POLAR_CUDA(cudaGetLastError());
+    return POLAR_OK;
 }
 
 int polar_profile_enable(int32_t on)

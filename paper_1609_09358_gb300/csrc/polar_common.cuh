@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -73,6 +74,26 @@ __device__ __forceinline__ void frame_sync(int slot)
         __syncwarp();
     } else {
         __syncthreads();
+    }
+}
+
+// compile-time loops: fn(integral_constant<int, i>) for i = I..E-1 (static_for) or I..E
+// descending (static_for_down); the index is a constant expression inside fn
+template <int I, int E, class Fn>
+__device__ __forceinline__ void static_for(Fn&& fn)
+{
+    if constexpr (I < E) {
+        fn(std::integral_constant<int, I>{});
+        static_for<I + 1, E>(fn);
+    }
+}
+
+template <int I, int E, class Fn>
+__device__ __forceinline__ void static_for_down(Fn&& fn)
+{
+    if constexpr (I >= E) {
+        fn(std::integral_constant<int, I>{});
+        static_for_down<I - 1, E>(fn);
     }
 }
 

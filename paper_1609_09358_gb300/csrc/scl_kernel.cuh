@@ -12,24 +12,24 @@
 // (metric, index) order -- the paper's pruned pseudo sort d = sum H(m_c - m_j) made a total order
 // by the index tie-break -- and the rank < L candidates survive, renumbered in ascending index.
 //
-// Lazy copy: every level k keeps L physical LLR arrays and L physical partial-sum arrays; a path
-// holds one 5-bit pointer per level, packed into two registers per table (lane = path).  A
-// surviving child copies only its parent's pointer words (four shuffles).  Since a level is always
-// rewritten whole, a path that is about to write a level it shares takes a free array of that
-// level instead (the lowest-numbered sharer keeps the old one): no LLR or partial-sum data is ever
-// copied.  A level is checked only if a list step duplicated a path since it was last written.
+// Leaf blocks in registers: the tree below level 6 is a 32-bit leaf block.  Lane p holds path p's
+// LLR arrays of levels 5..1 (62 values) and its partial sums of levels 0..4 (one word each) in
+// registers; the 32 bits of a block are unrolled, so every level index is a compile-time constant.
+// When a list step duplicates paths, a survivor copies from its parent's lane (shuffles) only the
+// leaf levels that a later bit of the block reads before rewriting -- a set known at compile time.
+//
+// Upper levels (LLR 6..n-1, partial sums 5..n) are touched once per block.  They use lazy copies:
+// every upper level keeps L physical arrays and a path holds one 5-bit pointer per level, packed in
+// two registers per table.  A survivor copies only its parent's pointer words; a path about to
+// rewrite a level it shares takes a free array of that level (the lowest-numbered sharer keeps the
+// old one), so no upper-level data is ever copied.  The small upper levels live in the warp's
+// shared memory, the large ones in its slot of the global workspace (L2-resident).
 //
 // Partial sums: after deciding bit i, the completed subtree re-encodes bottom-up,
 // v_{k+1} = (C_k xor v_k) || v_k, until the first level k where the completed node is a left
 // child (k = number of trailing ones of i); v_k is stored there.  After the last bit the level-n
 // array holds the path's codeword x, and u = x G (G is an involution) gives the decided bits for
 // the CRC check and the output.
-//
-// Storage: the small, hot levels (LLR levels 1..KS, partial sums 0..KC) sit in the warp's slice
-// of shared memory; the large upper levels, touched once per 2^k bits, sit in the warp's slot of
-// the global workspace (L2-resident).  This keeps ~10 KB of shared memory per warp, so that many
-// frames are in flight per SM -- the decoder is latency-bound (serial over the N bits).  With no
-// workspace every level is in shared memory (KS = n-1, KC = n).
 #pragma once
 
 #include <algorithm>
@@ -65,12 +65,15 @@ inline int log2_host(int v)
     return n;
 }
 
-// Host plan of the shared/global split for (N, L).
+// Host plan of the shared/global split of the upper levels for (N, L): LLR levels 6..KS and
+// partial-sum levels 5..KC in shared memory, the rest in the warp's global slot.
 struct SCLPlan {
     int KS, KC;
     int warp_words;
     long long slot_words;
 };
+__host__ __device__ inline long long scl_smem_llr_words(int KS, int L) { return KS >= 6 ? (long long)L * ((2 << KS) - 64) : 0; }
+__host__ __device__ inline long long scl_smem_c_words(int KC, int L) { return KC >= 5 ? (long long)L * (scl_cwsum(KC + 1) - 5) : 0; }
 inline SCLPlan scl_plan(int N, int L, bool all_smem)
 {
     const int n = log2_host(N);
@@ -79,12 +82,12 @@ inline SCLPlan scl_plan(int N, int L, bool all_smem)
         p.KS = n - 1;
         p.KC = n;
     } else {
-        p.KS = 1;
-        while (p.KS + 1 <= n - 1 && 4LL * L * ((2 << (p.KS + 1)) - 2) <= 8192) ++p.KS;
-        p.KC = 0;
-        while (p.KC + 1 <= n && 4LL * L * scl_cwsum(p.KC + 2) <= 3072) ++p.KC;
+        p.KS = 5;
+        while (p.KS + 1 <= n - 1 && 4 * scl_smem_llr_words(p.KS + 1, L) <= 6144) ++p.KS;
+        p.KC = 4;
+        while (p.KC + 1 <= n && 4 * scl_smem_c_words(p.KC + 1, L) <= 2048) ++p.KC;
     }
-    p.warp_words = L * scl_cwsum(p.KC + 1) + L * ((2 << p.KS) - 2) + 16;
+    p.warp_words = (int)(scl_smem_llr_words(p.KS, L) + scl_smem_c_words(p.KC, L)) + 16;
     p.warp_words = (p.warp_words + 3) & ~3;
     p.slot_words = (long long)L * (N - (2 << p.KS)) + (long long)L * (scl_cwsum(n + 1) - scl_cwsum(p.KC + 1));
     return p;
@@ -138,20 +141,179 @@ __device__ __forceinline__ void scl_own(uint32_t (&w)[2], int k, int act, int L)
 __device__ __forceinline__ float scl_g(float a, float b, uint32_t v) { return v ? __fsub_rn(b, a) : __fadd_rn(b, a); }
 
 struct SCLWarp {
-    float* sA;     // shared LLR levels 1..KS
-    uint32_t* sC;  // shared partial-sum levels 0..KC
+    float* sA;     // shared LLR levels 6..KS
+    uint32_t* sC;  // shared partial-sum levels 5..KC
     float* gA;     // global LLR levels KS+1..n-1
     uint32_t* gC;  // global partial-sum levels KC+1..n
     int L, KS, KC;
-    __device__ __forceinline__ float* A(int k) const
+    __device__ __forceinline__ float* A(int k) const  // k >= 6
     {
-        return k <= KS ? sA + L * ((1 << k) - 2) : gA + L * ((1 << k) - (2 << KS));
+        return k <= KS ? sA + L * ((1 << k) - 64) : gA + L * ((1 << k) - (2 << KS));
     }
-    __device__ __forceinline__ uint32_t* Cl(int k) const
+    __device__ __forceinline__ uint32_t* Cl(int k) const  // k >= 5
     {
-        return k <= KC ? sC + L * scl_cwsum(k) : gC + L * (scl_cwsum(k) - scl_cwsum(KC + 1));
+        return k <= KC ? sC + L * (scl_cwsum(k) - 5) : gC + L * (scl_cwsum(k) - scl_cwsum(KC + 1));
     }
 };
+
+// ------------------------------------------------------------------ leaf block (compile time)
+__host__ __device__ constexpr int ctz_c(int v)
+{
+    int c = 0;
+    while (!(v & 1)) {
+        v >>= 1;
+        ++c;
+    }
+    return c;
+}
+__host__ __device__ constexpr int tones_c(int v)  // trailing ones
+{
+    int c = 0;
+    while (v & 1) {
+        v >>= 1;
+        ++c;
+    }
+    return c;
+}
+// Is leaf level k (1..5) read, before being rewritten, by a later bit of the block than r?
+__host__ __device__ constexpr bool leaf_live(int r, int k)
+{
+    for (int q = r + 1; q < 32; ++q) {
+        const int t = ctz_c(q);
+        if (t + 1 == k) return true;
+        if (t >= k) return false;
+    }
+    return false;
+}
+
+template <int LEN>
+__device__ __forceinline__ void leaf_f(const float (&src)[2 * LEN], float (&dst)[LEN])
+{
+#pragma unroll
+    for (int j = 0; j < LEN; ++j) dst[j] = xmin(src[j], src[j + LEN]);
+}
+template <int LEN>
+__device__ __forceinline__ void leaf_g(const float (&src)[2 * LEN], float (&dst)[LEN], uint32_t c)
+{
+#pragma unroll
+    for (int j = 0; j < LEN; ++j) dst[j] = scl_g(src[j], src[j + LEN], (c >> j) & 1u);
+}
+template <int LEN>
+__device__ __forceinline__ void leaf_copy(float (&a)[LEN], int parent)
+{
+#pragma unroll
+    for (int j = 0; j < LEN; ++j) a[j] = __shfl_sync(0xffffffffu, a[j], parent);
+}
+
+struct Leaf {
+    float l5[32], l4[16], l3[8], l2[4], l1[2];
+    uint32_t c[5];  // partial sums of the left siblings at levels 0..4
+};
+
+// LLR of bit r of the block (levels written: ctz(r)..1, read: ctz(r)+1 and c[ctz(r)])
+template <int R>
+__device__ __forceinline__ float leaf_llr(Leaf& f)
+{
+    if constexpr (R == 0) {
+        leaf_f<16>(f.l5, f.l4);
+        leaf_f<8>(f.l4, f.l3);
+        leaf_f<4>(f.l3, f.l2);
+        leaf_f<2>(f.l2, f.l1);
+        return xmin(f.l1[0], f.l1[1]);
+    } else {
+        constexpr int t = ctz_c(R);
+        if constexpr (t == 4) leaf_g<16>(f.l5, f.l4, f.c[4]);
+        if constexpr (t == 3) leaf_g<8>(f.l4, f.l3, f.c[3]);
+        if constexpr (t == 2) leaf_g<4>(f.l3, f.l2, f.c[2]);
+        if constexpr (t == 1) leaf_g<2>(f.l2, f.l1, f.c[1]);
+        if constexpr (t == 0) return scl_g(f.l1[0], f.l1[1], f.c[0] & 1u);
+        if constexpr (t >= 4) leaf_f<8>(f.l4, f.l3);
+        if constexpr (t >= 3) leaf_f<4>(f.l3, f.l2);
+        if constexpr (t >= 2) leaf_f<2>(f.l2, f.l1);
+        return xmin(f.l1[0], f.l1[1]);
+    }
+}
+
+// after a duplicating list step at bit r: survivors take the live leaf state of their parents
+template <int R>
+__device__ __forceinline__ void leaf_inherit(Leaf& f, int parent)
+{
+    if constexpr (leaf_live(R, 5)) leaf_copy<32>(f.l5, parent);
+    if constexpr (leaf_live(R, 4)) leaf_copy<16>(f.l4, parent);
+    if constexpr (leaf_live(R, 3)) leaf_copy<8>(f.l3, parent);
+    if constexpr (leaf_live(R, 2)) leaf_copy<4>(f.l2, parent);
+    if constexpr (leaf_live(R, 1)) leaf_copy<2>(f.l1, parent);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) f.c[k] = __shfl_sync(0xffffffffu, f.c[k], parent);
+}
+
+// partial sums after bit r (value `bitv`): returns the level-5 value when the block completes
+template <int R>
+__device__ __forceinline__ uint32_t leaf_psum(Leaf& f, uint32_t bitv)
+{
+    constexpr int kc = tones_c(R);
+    uint32_t v = bitv;
+#pragma unroll
+    for (int k = 0; k < (kc < 5 ? kc : 5); ++k) {
+        const uint32_t m = (k == 4) ? 0xFFFFu : ((1u << (1 << k)) - 1u);
+        v = ((v ^ f.c[k]) & m) | ((v & m) << (1 << k));
+    }
+    if constexpr (kc < 5) f.c[kc] = v;
+    return v;
+}
+
+// One list step at an information bit: candidates, ranks, survivors.  Lane = path in and out;
+// returns the survivor's parent lane and decided bit, updates pm/act, reports duplication.
+template <bool TWO>
+__device__ __forceinline__ int scl_list_step(float lam, float& pm, int& act, int L, uint8_t* selc, uint32_t& bitv,
+                                             bool& dup)
+{
+    const int lane = threadIdx.x & 31;
+    const int nc = 2 * act;
+    float cm0, cm1 = 0.0f;
+    {
+        const float lp = __shfl_sync(0xffffffffu, lam, (lane >> 1) & 31);
+        const float pp = __shfl_sync(0xffffffffu, pm, (lane >> 1) & 31);
+        cm0 = ((uint32_t)(lane & 1) != (uint32_t)(lp < 0.0f)) ? __fadd_rn(pp, fabsf(lp)) : pp;
+    }
+    if constexpr (TWO) {
+        const float lp = __shfl_sync(0xffffffffu, lam, 16 + (lane >> 1));
+        const float pp = __shfl_sync(0xffffffffu, pm, 16 + (lane >> 1));
+        cm1 = ((uint32_t)(lane & 1) != (uint32_t)(lp < 0.0f)) ? __fadd_rn(pp, fabsf(lp)) : pp;
+    }
+    int rank0 = 0, rank1 = 0;
+    const int n0 = nc < 32 ? nc : 32;
+#pragma unroll 8
+    for (int c2 = 0; c2 < n0; ++c2) {
+        const float o = __shfl_sync(0xffffffffu, cm0, c2);
+        rank0 += (o < cm0) || (o == cm0 && c2 < lane);
+        if constexpr (TWO) rank1 += o <= cm1;  // every c2 < 32 precedes candidate lane + 32 on ties
+    }
+    if constexpr (TWO) {
+#pragma unroll 8
+        for (int c2 = 32; c2 < nc; ++c2) {
+            const float o = __shfl_sync(0xffffffffu, cm1, c2 - 32);
+            rank0 += o < cm0;
+            rank1 += (o < cm1) || (o == cm1 && c2 < lane + 32);
+        }
+    }
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t km0 = __ballot_sync(0xffffffffu, lane < nc && rank0 < L);
+    const uint32_t km1 = TWO ? __ballot_sync(0xffffffffu, lane + 32 < nc && rank1 < L) : 0u;
+    if (km0 & (1u << lane)) selc[__popc(km0 & below)] = (uint8_t)lane;
+    if (TWO && (km1 & (1u << lane))) selc[__popc(km0) + __popc(km1 & below)] = (uint8_t)(lane + 32);
+    dup = ((km0 & (km0 >> 1) & 0x55555555u) | (km1 & (km1 >> 1) & 0x55555555u)) != 0u;
+    const int nact = __popc(km0) + __popc(km1);
+    __syncwarp();
+    const int cq = lane < nact ? selc[lane] : 0;
+    __syncwarp();
+    const float m0 = __shfl_sync(0xffffffffu, cm0, cq & 31);
+    const float m1 = TWO ? __shfl_sync(0xffffffffu, cm1, cq & 31) : 0.0f;
+    bitv = (uint32_t)(cq & 1);
+    pm = lane < nact ? (cq < 32 ? m0 : m1) : 0.0f;
+    act = nact;
+    return cq >> 1;
+}
 
 template <bool TWO>  // TWO: L = 32, two candidates per lane
 __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, const SCLWarp& S, uint8_t* selc)
@@ -159,21 +321,24 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
     const int lane = threadIdx.x & 31;
     const int N = C.N, n = C.n, L = a.L;
     const float* y = a.llr + (size_t)frame * N;
-    uint32_t pA[2] = {0u, 0u}, pC[2] = {0u, 0u};  // pointer rows of path `lane`
-    float pm = 0.0f, lam = 0.0f;
+    uint32_t pA[2] = {0u, 0u}, pC[2] = {0u, 0u};  // upper-level pointer rows of path `lane`
+    float pm = 0.0f;
     int act = 1;
-    uint32_t shA = 0u, shC = 0u;  // levels that may be shared since the last duplication
-    uint32_t fw = 0u;
-    for (int i = 0; i < N; ++i) {
-        if ((i & 31) == 0) fw = C.frozen_bits[i >> 5];
-        const int t = i == 0 ? n : __ffs(i) - 1;
-        const int top = i == 0 ? n - 1 : t;
-        for (int k = top; k >= 1; --k) {
+    uint32_t shA = 0u, shC = 0u;  // upper levels that may be shared since the last duplication
+    Leaf lf;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) lf.c[k] = 0u;
+    const int nblocks = N >> 5;
+    for (int blk = 0; blk < nblocks; ++blk) {
+        // ------------------------------------------------ upper levels on entering the block
+        const int t = blk == 0 ? n : 5 + __ffs(blk) - 1;
+        const int top = blk == 0 ? n - 1 : t;
+        for (int k = top; k >= 6; --k) {
             if ((shA >> k) & 1u) {
                 scl_own(pA, k, act, L);
                 shA &= ~(1u << k);
             }
-            const bool use_g = i != 0 && k == t;
+            const bool use_g = blk != 0 && k == t;
             const bool from_ch = k + 1 == n;
             const int len = 1 << k;
             float* dst = S.A(k);
@@ -181,111 +346,84 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             const uint32_t* cbk = S.Cl(k);
             const uint32_t my_d = fld(pA, k), my_s = from_ch ? 0u : fld(pA, k + 1), my_c = fld(pC, k);
             const int cwk = scl_cw(k), total = act << k;
-            for (int e0 = 0; e0 < total; e0 += 32) {
-                const int e = e0 + lane;
-                const int p = (e >> k) & 31;
-                const uint32_t pd = __shfl_sync(0xffffffffu, my_d, p);
-                const uint32_t ps = __shfl_sync(0xffffffffu, my_s, p);
-                const uint32_t pc = __shfl_sync(0xffffffffu, my_c, p);
-                if (e < total) {
-                    const int j = e & (len - 1);
-                    const float* src = srcb + ps * (2 * len);
-                    const float va = src[j], vb = src[j + len];
-                    float r;
-                    if (use_g) {
-                        const uint32_t w = cbk[pc * cwk + (j >> 5)];
-                        r = scl_g(va, vb, (w >> (j & 31)) & 1u);
-                    } else {
-                        r = xmin(va, vb);
+            // four elements per lane per round: all loads of a round are issued before any store,
+            // so the L2 latency of the upper levels overlaps
+            for (int e0 = 0; e0 < total; e0 += 128) {
+                float va[4], vb[4];
+                uint32_t vw[4], pdv[4];
+                int jv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e = e0 + 32 * q + lane;
+                    const int p = (e >> k) & 31;
+                    pdv[q] = __shfl_sync(0xffffffffu, my_d, p);
+                    const uint32_t ps = __shfl_sync(0xffffffffu, my_s, p);
+                    const uint32_t pc = __shfl_sync(0xffffffffu, my_c, p);
+                    jv[q] = e & (len - 1);
+                    va[q] = vb[q] = 0.0f;
+                    vw[q] = 0u;
+                    if (e < total) {
+                        const float* src = srcb + ps * (2 * len);
+                        va[q] = src[jv[q]];
+                        vb[q] = src[jv[q] + len];
+                        if (use_g) vw[q] = cbk[pc * cwk + (jv[q] >> 5)];
                     }
-                    dst[pd * len + j] = r;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e = e0 + 32 * q + lane;
+                    if (e < total) {
+                        const float r = use_g ? scl_g(va[q], vb[q], (vw[q] >> (jv[q] & 31)) & 1u) : xmin(va[q], vb[q]);
+                        dst[pdv[q] * len + jv[q]] = r;
+                    }
                 }
             }
             __syncwarp();
         }
-        // bit LLR (level 0), lane = path
-        if (lane < act) {
-            const float* src = S.A(1) + fld(pA, 1) * 2;
-            const float va = src[0], vb = src[1];
-            if (i != 0 && t == 0)
-                lam = scl_g(va, vb, S.Cl(0)[fld(pC, 0)] & 1u);
-            else
-                lam = xmin(va, vb);
-        }
-        uint32_t bitv = 0u;
-        if ((fw >> (i & 31)) & 1u) {
-            if (lane < act && lam < 0.0f) pm = __fadd_rn(pm, fabsf(lam));
-        } else {
-            // ---------------------------------------------------------------- list step
-            const int nc = 2 * act;
-            float cm0, cm1 = 0.0f;
-            {
-                const float lp = __shfl_sync(0xffffffffu, lam, (lane >> 1) & 31);
-                const float pp = __shfl_sync(0xffffffffu, pm, (lane >> 1) & 31);
-                cm0 = ((uint32_t)(lane & 1) != (uint32_t)(lp < 0.0f)) ? __fadd_rn(pp, fabsf(lp)) : pp;
-            }
-            if constexpr (TWO) {
-                const float lp = __shfl_sync(0xffffffffu, lam, 16 + (lane >> 1));
-                const float pp = __shfl_sync(0xffffffffu, pm, 16 + (lane >> 1));
-                cm1 = ((uint32_t)(lane & 1) != (uint32_t)(lp < 0.0f)) ? __fadd_rn(pp, fabsf(lp)) : pp;
-            }
-            int rank0 = 0, rank1 = 0;
-            const int n0 = nc < 32 ? nc : 32;
-            for (int c2 = 0; c2 < n0; ++c2) {
-                const float o = __shfl_sync(0xffffffffu, cm0, c2);
-                rank0 += (o < cm0) || (o == cm0 && c2 < lane);
-                if constexpr (TWO) rank1 += o <= cm1;  // every c2 < 32 precedes candidate lane + 32 on ties
-            }
-            if constexpr (TWO) {
-                for (int c2 = 32; c2 < nc; ++c2) {
-                    const float o = __shfl_sync(0xffffffffu, cm1, c2 - 32);
-                    rank0 += o < cm0;
-                    rank1 += (o < cm1) || (o == cm1 && c2 < lane + 32);
-                }
-            }
-            const uint32_t below = (1u << lane) - 1u;
-            const uint32_t km0 = __ballot_sync(0xffffffffu, lane < nc && rank0 < L);
-            const uint32_t km1 = TWO ? __ballot_sync(0xffffffffu, lane + 32 < nc && rank1 < L) : 0u;
-            if (km0 & (1u << lane)) selc[__popc(km0 & below)] = (uint8_t)lane;
-            if (TWO && (km1 & (1u << lane))) selc[__popc(km0) + __popc(km1 & below)] = (uint8_t)(lane + 32);
-            const bool dup = ((km0 & (km0 >> 1) & 0x55555555u) | (km1 & (km1 >> 1) & 0x55555555u)) != 0u;
-            const int nact = __popc(km0) + __popc(km1);
-            __syncwarp();
-            const int cq = lane < nact ? selc[lane] : 0;
-            __syncwarp();
-            const float m0 = __shfl_sync(0xffffffffu, cm0, cq & 31);
-            const float m1 = TWO ? __shfl_sync(0xffffffffu, cm1, cq & 31) : 0.0f;
-            const int parent = cq >> 1;
-            bitv = (uint32_t)(cq & 1);
-            // pointer rows of the survivors: their parents' rows
-            pA[0] = __shfl_sync(0xffffffffu, pA[0], parent);
-            pA[1] = __shfl_sync(0xffffffffu, pA[1], parent);
-            pC[0] = __shfl_sync(0xffffffffu, pC[0], parent);
-            pC[1] = __shfl_sync(0xffffffffu, pC[1], parent);
-            pm = lane < nact ? (cq < 32 ? m0 : m1) : 0.0f;
-            act = nact;
-            if (dup) shA = shC = 0xffffffffu;
-        }
-        // -------------------------------------------------------------- partial sums
-        const int kc = __ffs(~i) - 1;  // trailing ones of i; n after the last bit
-        if ((shC >> kc) & 1u) {
-            scl_own(pC, kc, act, L);
-            shC &= ~(1u << kc);
-        }
+        // level 5 of every path into its lane's registers (from level 6 or the channel)
         {
+            const bool use_g5 = blk != 0 && t == 5;
+            const float* src = (n == 6) ? y : S.A(6) + fld(pA, 6) * 64;
+            const uint32_t c5 = use_g5 ? S.Cl(5)[fld(pC, 5)] : 0u;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float va = src[j], vb = src[j + 32];
+                lf.l5[j] = use_g5 ? scl_g(va, vb, (c5 >> j) & 1u) : xmin(va, vb);
+            }
+        }
+        // ------------------------------------------------ the 32 bits of the block, unrolled
+        const uint32_t fw = C.frozen_bits[blk];
+        uint32_t v5 = 0u;
+        static_for<0, 32>([&](auto RC) {
+            constexpr int r = RC.value;
+            const float lam = leaf_llr<r>(lf);
+            uint32_t bitv = 0u;
+            if ((fw >> r) & 1u) {
+                if (lane < act && lam < 0.0f) pm = __fadd_rn(pm, fabsf(lam));
+            } else {
+                bool dup = false;
+                const int parent = scl_list_step<TWO>(lam, pm, act, L, selc, bitv, dup);
+                leaf_inherit<r>(lf, parent);
+                pA[0] = __shfl_sync(0xffffffffu, pA[0], parent);
+                pA[1] = __shfl_sync(0xffffffffu, pA[1], parent);
+                pC[0] = __shfl_sync(0xffffffffu, pC[0], parent);
+                pC[1] = __shfl_sync(0xffffffffu, pC[1], parent);
+                if (dup) shA = shC = 0xffffffffu;
+            }
+            const uint32_t v = leaf_psum<r>(lf, bitv);
+            if constexpr (r == 31) v5 = v;
+        });
+        // ------------------------------------------------ block complete: partial sums upward
+        {
+            const int i_last = blk * 32 + 31;
+            const int kc = __ffs(~i_last) - 1;  // >= 5; n after the last block
+            if ((shC >> kc) & 1u) {
+                scl_own(pC, kc, act, L);
+                shC &= ~(1u << kc);
+            }
             uint32_t* dstl = S.Cl(kc);
             const int cwk = scl_cw(kc);
-            // bottom five levels in one word per path (lane = path)
-            uint32_t v = bitv;
-            const int kw = kc < 5 ? kc : 5;
-            if (lane < act) {
-                for (int k = 0; k < kw; ++k) {
-                    const uint32_t ck = S.Cl(k)[fld(pC, k)];
-                    const uint32_t m = (1u << (1 << k)) - 1u;
-                    v = ((v ^ ck) & m) | ((v & m) << (1 << k));
-                }
-                dstl[fld(pC, kc) * cwk] = v;
-            }
+            if (lane < act) dstl[fld(pC, kc) * cwk] = v5;
             __syncwarp();
             const uint32_t my_dst = fld(pC, kc);
             for (int k = 5; k < kc; ++k) {
@@ -397,7 +535,7 @@ __global__ void __launch_bounds__(kSclWarpsPerCTA * 32) scl_kernel(const SCLArgs
     S.KS = a.KS;
     S.KC = a.KC;
     S.sC = ws;
-    S.sA = reinterpret_cast<float*>(ws + L * scl_cwsum(a.KC + 1));
+    S.sA = reinterpret_cast<float*>(ws + scl_smem_c_words(a.KC, L));
     uint8_t* selc = reinterpret_cast<uint8_t*>(ws + a.warp_words - 16);
     float* slot = a.scratch ? a.scratch + ((size_t)blockIdx.x * (blockDim.x >> 5) + wid) * (size_t)a.slot_words : nullptr;
     S.gA = slot;

@@ -1,0 +1,134 @@
+"""Learned weighted min-sum BP: per-edge, per-iteration scale factors trained by gradient descent.
+
+The weighted BP multiplies every g term of the BP update (Sec. II-B) by a learned scale
+w[t][dir][s-1][node] (dir 0: R message, 1: L message; node: the output node).  Forward and backward
+are the hand-written CUDA kernels behind `wms_forward` / `wms_backward` of the C ABI; this module
+only wires them into torch.autograd, draws training frames with the library's generator (Eb/N0
+uniform per frame), and runs an optimiser.  Inference with trained weights goes through
+`bp_decode` / `hybrid_decode` (wms_scales), with CRC early stop and CA-SCL as fallback.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import torch
+
+from . import api
+
+
+class WMSFunction(torch.autograd.Function):
+    """LLR(u) [B][N] of T weighted BP iterations; gradient w.r.t. the weights [T][2][n][N]."""
+
+    @staticmethod
+    def forward(ctx, w, llr, code, T, llr_max):
+        B, N = llr.shape
+        ws = torch.empty(api.wms_workspace_bytes(code, B, T), dtype=torch.uint8, device=llr.device)
+        out = torch.empty((B, N), dtype=torch.float32, device=llr.device)
+        w = w.detach().contiguous()
+        api.wms_forward(code, llr, T, llr_max, w, out, ws)
+        ctx.save_for_backward(w, llr)
+        ctx.ws, ctx.code, ctx.T, ctx.llr_max = ws, code, T, llr_max
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        w, llr = ctx.saved_tensors
+        grad_w = torch.empty_like(w)
+        api.wms_backward(ctx.code, llr, ctx.T, ctx.llr_max, w, grad_out.contiguous(), grad_w, ctx.ws)
+        ctx.ws = None
+        return grad_w, None, None, None, None
+
+
+def wms_llr_u(w, llr, code: api.PolarCode, T: int, llr_max: float = 20.0):
+    return WMSFunction.apply(w, llr, code, T, llr_max)
+
+
+def bce_loss(llr_u, u_info_sign, info_idx):
+    """Mean binary cross-entropy of the information bits: softplus(-s * LLR) with s = 1 - 2u."""
+    y = llr_u[:, info_idx]
+    return torch.nn.functional.softplus(-u_info_sign * y).mean()
+
+
+class FrameSource:
+    """Seeded training batches from the library's generator kernels (Eb/N0 uniform per frame)."""
+
+    def __init__(self, code: api.PolarCode, batch: int, ebn0_range=(1.0, 4.0), seed: int = 1609093583,
+                 device="cuda"):
+        self.code, self.B, self.lo, self.hi, self.seed = code, batch, ebn0_range[0], ebn0_range[1], seed
+        self.dev = torch.device(device)
+        self.gen = torch.Generator(device=self.dev)
+        self.gen.manual_seed(seed)
+        self.payload = torch.empty((batch, code.row_bytes), dtype=torch.uint8, device=self.dev)
+        self.cw = torch.empty((batch, code.N // 8), dtype=torch.uint8, device=self.dev)
+        self.llr = torch.empty((batch, code.N), dtype=torch.float32, device=self.dev)
+        self.frame = 0
+        self.info = torch.as_tensor(code.info_idx, dtype=torch.long, device=self.dev)
+
+    def next(self):
+        c = self.code
+        api.polar_random_payload(self.B, c.P, self.seed, self.frame, self.payload)
+        api.polar_encode(c, self.payload, self.cw)
+        ebn0 = self.lo + (self.hi - self.lo) * torch.rand(self.B, generator=self.gen, device=self.dev)
+        sig = torch.sqrt(1.0 / (2.0 * (c.P / c.N) * torch.pow(10.0, ebn0 / 10.0))).float().contiguous()
+        api.polar_awgn_llr(self.cw, c.N, 1.0, self.seed, self.frame, self.llr, sigma_per_frame=sig)
+        self.frame += self.B
+        # bits of the information positions: x = u G, u = x G; read u back from the codeword
+        bits = self.cw.unsqueeze(-1).bitwise_right_shift(torch.arange(8, device=self.dev, dtype=torch.uint8))
+        x = (bits & 1).reshape(self.B, c.N)
+        u = polar_transform_bits(x)
+        sign = 1.0 - 2.0 * u[:, self.info].float()
+        return self.llr, sign
+
+
+def polar_transform_bits(x):
+    """u = x G over GF(2) for a [B][N] 0/1 tensor (G is an involution); used for training labels."""
+    u = x.clone()
+    N = u.shape[1]
+    d = 1
+    while d < N:
+        v = u.view(u.shape[0], N // (2 * d), 2, d)
+        v[:, :, 0, :] ^= v[:, :, 1, :]
+        d *= 2
+    return u
+
+
+def train(code: api.PolarCode, T: int = 20, steps: int = 300, batch: int = 4096, lr: float = 3e-3,
+          ebn0_range=(1.0, 4.0), llr_max: float = 20.0, seed: int = 1609093583, log_every: int = 50,
+          w0=None, device="cuda"):
+    """Adam on the BCE of the information bits of LLR(u) after T iterations; returns (w, history)."""
+    torch.manual_seed(seed)
+    n, N = code.n, code.N
+    w = (torch.ones((T, 2, n, N), dtype=torch.float32, device=device) if w0 is None else w0.clone().to(device))
+    w.requires_grad_(True)
+    opt = torch.optim.Adam([w], lr=lr)
+    src = FrameSource(code, batch, ebn0_range, seed, device)
+    hist = []
+    for step in range(steps):
+        llr, sign = src.next()
+        y = wms_llr_u(w, llr, code, T, llr_max)
+        loss = bce_loss(y, sign, src.info)
+        opt.zero_grad(set_to_none=True)
+        loss.backward()
+        opt.step()
+        with torch.no_grad():
+            w.clamp_(0.0, 4.0)
+        if step % log_every == 0 or step == steps - 1:
+            hist.append((step, float(loss.item())))
+    return w.detach(), hist
+
+
+def save(path: str, w, code: api.PolarCode, T: int, meta: dict | None = None) -> None:
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    torch.save({"w": w.cpu(), "N": code.N, "K": code.K, "crc_len": code.crc_len, "T": T,
+                "frozen": torch.as_tensor(code.frozen), "meta": meta or {}}, path)
+
+
+def load(path: str, device="cuda"):
+    d = torch.load(path, map_location="cpu")
+    code = api.PolarCode(d["N"], d["K"], d["crc_len"], d["frozen"].numpy())
+    return d["w"].to(device), code, d["T"], d.get("meta", {})
+
+
+def sigma_of(ebn0_db: float, rate: float) -> float:
+    return math.sqrt(1.0 / (2.0 * rate * 10.0 ** (ebn0_db / 10.0)))

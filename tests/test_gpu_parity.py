@@ -290,3 +290,18 @@ def test_profiling_hooks_count_launches():
     bp_ms, bp_n, scl_ms, scl_n = api.polar_profile_read()
     assert bp_n == 3 and scl_n == 3 and bp_ms > 0 and scl_ms > 0
     assert api.polar_profile_read()[1] == 0
+
+
+def test_hybrid_multi_chunk_every_frame():
+    """A batch of several hybrid chunks (BP chunks on two streams, CA-SCL of each chunk
+    concurrent with later BP chunks), at an Eb/N0 where a large share of frames falls back: every
+    frame is compared with the oracle."""
+    ocode = fr.oracle_code(128, 64, 8)
+    B = 40_000
+    _, llr = fr.frames_large(ocode, 1.0, B, seed=606)
+    ref = oracle.hybrid_decode(llr, ocode, 30, 20.0, 4, precision="f32")
+    bits, status, iters, nfb = run_hybrid(ocode, llr, 30, 4)
+    assert nfb == int(np.sum(ref["status"] != oracle.BP_OK)) > 1000
+    assert np.array_equal(iters, ref["iters"])
+    assert np.array_equal(status, ref["status"])
+    assert np.array_equal(bits, oracle.payload_of(ref["u_hat"], ocode))

@@ -370,3 +370,35 @@ def test_scl_path_metric_is_discrepancy_for_any_list():
             assert ok and np.array_equal(u, lst[passing[0]])
         else:
             assert not ok and np.array_equal(u, lst[int(np.argmin(pms))])
+
+
+@pytest.mark.parametrize("N,T", [(16, 3), (32, 2)])
+def test_wms_gradient_matches_central_differences(N, T):
+    """The oracle's reverse sweep of the weighted BP equals central differences of its FP64
+    forward (the loss sum_i dy_i LLR(u_i) is linear in the output, so only the BP is tested)."""
+    frozen, info, _ = oracle.construct(N, N // 2, 0.0, 0.5)
+    code = oracle.Code(N, N // 2, 0, 0, frozen, info)
+    rng = np.random.default_rng(N)
+    llr = rng.normal(1.5, 2.0, (2, N)).astype(np.float32)
+    w = rng.uniform(0.7, 1.3, (T, 2, code.n, N)).astype(np.float32)
+    dy = rng.normal(size=(2, N))
+
+    def f(ww):
+        y = oracle.bp_decode(llr, code, T, 20.0, "f64", early_stop=False, w=ww, llr_u_double=True)["llr_u_f64"]
+        return float(np.sum(dy * y))
+
+    g = oracle.wms_grad(llr, code, T, 20.0, w, dy, "f64")
+    assert np.abs(g).max() > 0
+    h = 1e-6
+    idx = np.argsort(-np.abs(g).ravel())[:6].tolist() + rng.choice(w.size, 6, replace=False).tolist()
+    for i in idx:
+        wp, wm = w.copy(), w.copy()
+        wp.flat[i] += h
+        wm.flat[i] -= h
+        fd = (f(wp) - f(wm)) / (float(wp.flat[i]) - float(wm.flat[i]))
+        assert fd == pytest.approx(g.flat[i], rel=1e-6, abs=1e-9), i
+    for _ in range(3):
+        v = rng.choice([-1.0, 1.0], size=w.shape)
+        wp, wm = (w + h * v).astype(np.float32), (w - h * v).astype(np.float32)
+        fd = f(wp) - f(wm)
+        assert fd == pytest.approx(float(np.sum(g * (wp.astype(np.float64) - wm.astype(np.float64)))), rel=1e-5, abs=1e-12)
