@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=100_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1609_09358_gb300", "weights", "wms_n1024_k512_t20.pt"))
     return ap.parse_args()
 
 
@@ -301,6 +303,8 @@ def main():
             "bp_ms_per_step": bp_ms / a.steps, "scl_ms_per_step": scl_ms / a.steps,
             "gpu_launches": bp_n + scl_n, "roofline": roofline, "clocks": clocks}
 
+    if not a.no_learned and os.path.exists(a.weights):
+        line["learned_fp16"] = learned(a, llr, payload, stream, dist)
     if not a.no_e2e:
         line["e2e"] = e2e(a, code, llr, prec, llr_max, dev, stream, dist)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -313,6 +317,47 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def learned(a, llr, payload, stream, dist):
+    """The learned/FP16 form on the same frames: half2 BP with the trained per-edge weights,
+    T = 20 iterations with CRC early stop, then CA-SCL L = 8 on the CRC failures."""
+    import torch
+
+    from paper_1609_09358_gb300 import api, wms
+    w, lcode, T, meta = wms.load(a.weights, device=llr.device)
+    B = llr.shape[0]
+    dec = api.Decoder(lcode, B, LIST, device=llr.device)
+
+    def step():
+        dec.hybrid(llr, T, 32.0, api.POLAR_FP16, w)
+
+    for _ in range(max(a.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    steps = max(1, min(a.steps, 50))
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    api.polar_profile_enable(True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    api.polar_profile_enable(False)
+    bp_ms, _, scl_ms, _ = api.polar_profile_read()
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=llr.device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    world = dist.get_world_size() if dist else 1
+    ferr = (dec.bits != payload).any(dim=1)
+    return {"value": world * lcode.P * B * steps / (float(t.item()) * 1e-3) / 1e9, "unit": "Gbit/s", "steps": steps,
+            "ms_per_step": float(t.item()) / steps, "fer": float(ferr.float().mean().item()),
+            "fallback_rate": float((dec.status != api.FRAME_BP_OK).float().mean().item()),
+            "avg_bp_iters": float(dec.iters.float().mean().item()), "i_max": T,
+            "bp_ms_per_step": bp_ms / steps, "scl_ms_per_step": scl_ms / steps, "dtype": "f16",
+            "weights": os.path.relpath(a.weights, ROOT), "training": {k: meta.get(k) for k in ("steps", "batch", "lr")}}
 
 
 def e2e(a, code, llr, prec, llr_max, dev, stream, dist):

@@ -162,6 +162,37 @@ int wms_backward(const polar_code* code, const float* llr, int32_t B, int32_t T,
                  const float* w, const float* grad_llr_u, float* grad_w, void* workspace,
                  size_t ws_bytes, void* stream);
 
+/* Mixed batch (the configurations' mixed workload; not in the paper): frames of up to
+ * POLAR_MAX_MIX_CODES codes of different lengths and rates in one batch.  Frames are bucketed by
+ * code on the device, then one persistent BP launch decodes all of them (a CTA works on one code
+ * at a time and moves to the next when that code's queue is empty) and one CA-SCL launch decodes
+ * every frame whose CRC failed, each with its own code.  Nothing waits for the host, so the call
+ * can be captured in a CUDA graph once each code has been used (code tables uploaded) and
+ * polar_mixed_autotune has run.  Results equal hybrid_decode of each frame with its own code.
+ *   codes: host array of ncodes code descriptions.  code_of: device int32 [B], code of each frame
+ *   (a frame with a code id outside [0, ncodes) is not decoded and its outputs are not written).
+ *   llr_off: device int64 [B], element offset of each frame's LLR row in llr (device float).
+ *   bits: device [B][row_stride], row_stride >= ceil(P/8) of every code; status, iters: [B].
+ *   workspace: device, >= polar_mixed_workspace_bytes(codes, ncodes, B, L). */
+#define POLAR_MAX_MIX_CODES 32
+size_t polar_mixed_workspace_bytes(const polar_code* codes, int32_t ncodes, int32_t B, int32_t L);
+int hybrid_decode_mixed(const polar_code* codes, int32_t ncodes, const int32_t* code_of,
+                        const int64_t* llr_off, const float* llr, int32_t B, int32_t max_iters,
+                        float llr_max, int32_t precision, int32_t L, uint8_t* bits,
+                        int32_t row_stride, uint8_t* status, uint16_t* iters, void* workspace,
+                        size_t ws_bytes, void* stream);
+/* Autotuner of the mixed BP launch: for the block lengths that have two BP thread plans (256 and
+ * 512: 8 or 4 nodes per thread, i.e. twice or half as many frames per CTA) it times the BP launch
+ * on this batch with each choice and keeps the fastest for later hybrid_decode_mixed calls of the
+ * same precision.  Synchronises `stream`; overwrites the outputs.  Arguments as in
+ * hybrid_decode_mixed.  *chosen (host, may be NULL) receives the plan flags (bit 0: N = 256 uses 4
+ * nodes per thread, bit 1: N = 512 does), *best_ms the BP time of the chosen plans. */
+int polar_mixed_autotune(const polar_code* codes, int32_t ncodes, const int32_t* code_of,
+                         const int64_t* llr_off, const float* llr, int32_t B, int32_t max_iters,
+                         float llr_max, int32_t precision, uint8_t* bits, int32_t row_stride,
+                         uint8_t* status, uint16_t* iters, void* workspace, size_t ws_bytes,
+                         void* stream, int32_t* chosen, float* best_ms);
+
 /* hybrid_decode on frames that live in host memory (not a step of the paper; its Sec. III
  * rejects moving SCL to the CPU because of transfer latency, which is what this hides).  The
  * batch is cut into chunks of up to POLAR_HOST_CHUNK frames; each chunk's LLRs are copied to the

@@ -55,6 +55,11 @@ SIGNATURES = {
                                           _sz, _vp]),
     "hybrid_decode_noalloc": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _i32, _vp, _i32, _i32, _vp, _vp, _vp,
                                              _vp]),
+    "polar_mixed_workspace_bytes": (_sz, [_CP, _i32, _i32, _i32]),
+    "hybrid_decode_mixed": (ctypes.c_int, [_CP, _i32, _vp, _vp, _vp, _i32, _i32, _f32, _i32, _i32, _vp, _i32, _vp, _vp,
+                                           _vp, _sz, _vp]),
+    "polar_mixed_autotune": (ctypes.c_int, [_CP, _i32, _vp, _vp, _vp, _i32, _i32, _f32, _i32, _vp, _i32, _vp, _vp,
+                                            _vp, _sz, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_f32)]),
     "polar_profile_enable": (ctypes.c_int, [_i32]),
     "polar_profile_read": (ctypes.c_int, [ctypes.POINTER(_f64), ctypes.POINTER(_i32), ctypes.POINTER(_f64),
                                           ctypes.POINTER(_i32)]),
@@ -306,3 +311,79 @@ def pack_bits(bits: np.ndarray) -> np.ndarray:
     """uint8 [B][nbits] (one byte per bit) -> [B][ceil(nbits/8)] little-endian packed bytes."""
     bits = np.asarray(bits, dtype=np.uint8)
     return np.packbits(bits, axis=1, bitorder="little")
+
+
+# ------------------------------------------------------------------------ mixed batches
+def _code_array(codes):
+    arr = (_PolarCode * len(codes))(*[c._c for c in codes])
+    return arr
+
+
+def polar_mixed_workspace_bytes(codes, B: int, L: int) -> int:
+    arr = _code_array(codes)
+    return int(load().polar_mixed_workspace_bytes(arr, len(codes), B, L))
+
+
+def hybrid_decode_mixed(codes, code_of, llr_off, llr, max_iters: int, llr_max: float, precision: int, L: int, bits,
+                        status, iters, workspace, stream=None) -> None:
+    """One batch of frames of several codes; code_of int32 [B], llr_off int64 [B] (CUDA tensors)."""
+    arr = _code_array(codes)
+    B = code_of.shape[0]
+    ws_b = workspace.numel() * workspace.element_size()
+    _check(load().hybrid_decode_mixed(arr, len(codes), _ptr(code_of), _ptr(llr_off), _ptr(llr), B, max_iters,
+                                      llr_max, precision, L, _ptr(bits), bits.shape[1], _ptr(status), _ptr(iters),
+                                      _ptr(workspace), ws_b, _stream(stream)), "hybrid_decode_mixed")
+
+
+def polar_mixed_autotune(codes, code_of, llr_off, llr, max_iters: int, llr_max: float, precision: int, bits, status,
+                         iters, workspace, stream=None):
+    arr = _code_array(codes)
+    B = code_of.shape[0]
+    ws_b = workspace.numel() * workspace.element_size()
+    chosen, best = _i32(0), _f32(0)
+    _check(load().polar_mixed_autotune(arr, len(codes), _ptr(code_of), _ptr(llr_off), _ptr(llr), B, max_iters,
+                                       llr_max, precision, _ptr(bits), bits.shape[1], _ptr(status), _ptr(iters),
+                                       _ptr(workspace), ws_b, _stream(stream), ctypes.byref(chosen),
+                                       ctypes.byref(best)), "polar_mixed_autotune")
+    return int(chosen.value), float(best.value)
+
+
+class MixedDecoder:
+    """Buffers and workspace for mixed batches of a fixed code set and batch size; `capture()`
+    records one decode into a CUDA graph that `replay()` relaunches."""
+
+    def __init__(self, codes, B: int, L: int = 8, device="cuda"):
+        import torch
+        self.codes, self.B, self.L = list(codes), B, L
+        self.row = max(c.row_bytes for c in self.codes)
+        self.bits = torch.zeros((B, self.row), dtype=torch.uint8, device=device)
+        self.status = torch.zeros(B, dtype=torch.uint8, device=device)
+        self.iters = torch.zeros(B, dtype=torch.int16, device=device)
+        self.workspace = torch.zeros(polar_mixed_workspace_bytes(self.codes, B, L), dtype=torch.uint8, device=device)
+        self.graph = None
+
+    def decode(self, code_of, llr_off, llr, max_iters: int, llr_max: float = 20.0, precision: int = POLAR_FP32,
+               stream=None):
+        hybrid_decode_mixed(self.codes, code_of, llr_off, llr, max_iters, llr_max, precision, self.L, self.bits,
+                            self.status, self.iters, self.workspace, stream)
+        return self.bits, self.status, self.iters
+
+    def autotune(self, code_of, llr_off, llr, max_iters: int, llr_max: float = 20.0, precision: int = POLAR_FP32):
+        return polar_mixed_autotune(self.codes, code_of, llr_off, llr, max_iters, llr_max, precision, self.bits,
+                                    self.status, self.iters, self.workspace)
+
+    def capture(self, code_of, llr_off, llr, max_iters: int, llr_max: float = 20.0, precision: int = POLAR_FP32):
+        import torch
+        self.decode(code_of, llr_off, llr, max_iters, llr_max, precision)  # uploads code tables first
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.decode(code_of, llr_off, llr, max_iters, llr_max, precision, stream=s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+        return self.bits, self.status, self.iters

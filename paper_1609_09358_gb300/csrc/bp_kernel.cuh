@@ -116,6 +116,7 @@ struct BPArgs {
     int* fail_list;
     int* fail_total;  // optional running total of CRC-failed frames
     int* next;        // work counter (zero before the launch): groups refill from it; null = one frame group per CTA slot
+    const long long* llr_off;  // element offset of each frame's LLR row (null: frame * N)
     int row_bytes;
 };
 
@@ -164,6 +165,63 @@ struct MsgTraits<__half2> {
     __device__ static __half2 pair(float a, float b) { return __floats2half2_rn(a, b); }
 };
 
+// Barrier of one frame group: the warp (T <= 32), the whole CTA (the group owns its CTA), or a
+// named barrier (several groups wider than a warp share the CTA; ids 1.. by slot).
+template <int T, bool SHARED_CTA>
+__device__ __forceinline__ void group_sync(int slot)
+{
+    if constexpr (T <= 32) {
+        __syncwarp();
+    } else if constexpr (!SHARED_CTA) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(slot + 1), "r"(T) : "memory");
+    }
+}
+
+// Frame source of the per-length kernel: the group's own frames (no counter) or a work counter.
+struct CounterSource {
+    int* next;
+    int B;
+    int first;  // first static frame of the group
+    int FPT;
+    int nfetch = 0;
+    template <int T, bool SHARED_CTA>
+    __device__ int fetch(int slot, int t, int* cell)
+    {
+        int f;
+        if (next) {
+            if (t == 0) cell[0] = atomicAdd(next, 1);
+            group_sync<T, SHARED_CTA>(slot);
+            f = cell[0];
+            group_sync<T, SHARED_CTA>(slot);
+        } else {
+            f = nfetch < FPT ? first + nfetch : B;
+        }
+        ++nfetch;
+        return f < B ? f : -1;
+    }
+};
+
+// Frame source of the mixed-length kernel: a queue of frame indices of one code.
+struct QueueSource {
+    const int* list;
+    int count;
+    int* next;
+    template <int T, bool SHARED_CTA>
+    __device__ int fetch(int slot, int t, int* cell)
+    {
+        if (t == 0) {
+            const int k = atomicAdd(next, 1);
+            cell[0] = k < count ? list[k] : -1;
+        }
+        group_sync<T, SHARED_CTA>(slot);
+        const int f = cell[0];
+        group_sync<T, SHARED_CTA>(slot);
+        return f;
+    }
+};
+
 template <int LOGN>
 struct BPConfig;  // thread plan and frames (or frame pairs) per CTA for each block length
 template <> struct BPConfig<7>  { using Plan = BPPlan<7, 2>;  static constexpr int F = 4; };
@@ -180,54 +238,35 @@ __host__ __device__ constexpr int bp_slot_words()
     return 2 * P::N + P::N + 4 * P::NW + 2 * (P::N / 32) + 4;
 }
 
-// THREADS = F * T (passed explicitly: launch bounds take no dependent member expression)
-template <int LOGN, class MSG, bool WEIGHTED, int THREADS>
-__global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
+// One frame group of T threads decoding frames from `src` until it runs dry.  Group `slot` of
+// the CTA uses the shared-memory slice `slot_smem` (bp_slot_words<P>() words).
+template <class P, class MSG, bool WEIGHTED, bool SHARED_CTA, class Src>
+__device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, int slot, int t, uint32_t* slot_smem,
+                                             Src& src)
 {
-    using P = typename BPConfig<LOGN>::Plan;
     using MT = MsgTraits<MSG>;
-    constexpr int F = BPConfig<LOGN>::F;
-    constexpr int N = P::N, R = P::R, T = P::T, NG = P::NG, NW = P::NW, n = LOGN;
+    constexpr int N = P::N, R = P::R, T = P::T, NG = P::NG, NW = P::NW, n = P::LOGN;
     constexpr int FPT = MT::FPT;
-    constexpr int SW = bp_slot_words<P>();
-    static_assert(THREADS == F * T, "launch shape");
-    static_assert(T <= 32 || F == 1, "frame groups wider than a warp own their CTA");
     static_assert(plan_is_conflict_free<P>(), "exchange layout has bank conflicts");
     // exchanges alternate between the two buffers; an even count per iteration keeps the
     // alternation across iterations, so a buffer is rewritten only after a barrier that follows
     // every read of its previous contents
     static_assert(P::xidx_l(0) % 2 == 0, "odd number of exchanges per iteration");
 
-    extern __shared__ uint32_t smem[];
-    const int slot = threadIdx.x / T;
-    const int t = threadIdx.x % T;
-    MSG* xbuf = reinterpret_cast<MSG*>(smem + slot * SW);  // [2][N]; half2 uses the first half
-    uint32_t* csyn = smem + slot * SW + 2 * N;             // [R][T]
+    MSG* xbuf = reinterpret_cast<MSG*>(slot_smem);         // [2][N]; half2 uses the first half
+    uint32_t* csyn = slot_smem + 2 * N;                    // [R][T]
     uint32_t* synp = csyn + N;                             // [2 parity][2 frame][NW]
     uint32_t* pbits = synp + 4 * NW;                       // [2 frame][N/32]
     int* fetched = reinterpret_cast<int*>(pbits + 2 * (N / 32));
 
     // Frames of this group: half h (h < FPT) decodes frame fr[h]; when it stops it fetches the
-    // next frame from the work counter (or, without one, the group's single static frame group).
-    int nfetch = 0;
-    auto fetch = [&]() -> int {
-        int f;
-        if (a.next) {
-            if (t == 0) fetched[0] = atomicAdd(a.next, 1);
-            frame_sync<T>(slot);
-            f = fetched[0];
-            frame_sync<T>(slot);
-        } else {
-            f = nfetch < FPT ? (blockIdx.x * F + slot) * FPT + nfetch : a.B;
-        }
-        ++nfetch;
-        return f < a.B ? f : -1;
-    };
+    // next frame from the source.
+    auto fetch = [&]() -> int { return src.template fetch<T, SHARED_CTA>(slot, t, fetched); };
+    auto row = [&](int f) -> const float* { return a.llr + (a.llr_off ? a.llr_off[f] : (long long)f * N); };
     int fr[2] = {-1, -1}, itc[2] = {0, 0};
     fr[0] = fetch();
     if constexpr (FPT == 2) fr[1] = fetch();
     if (fr[0] < 0 && fr[1] < 0) return;  // uniform over the group
-    const DevCode& C = *a.code;
     const float M = a.llr_max;
     const MSG Mv = MT::splat(M);
 
@@ -240,8 +279,8 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
         Rc[1][k] = frozen_at(C.frozen_bits, j) ? Mv : MT::splat(0.0f);
     }
     {
-        const float* y0 = fr[0] >= 0 ? a.llr + (size_t)fr[0] * N : nullptr;
-        const float* y1 = fr[1] >= 0 ? a.llr + (size_t)fr[1] * N : nullptr;
+        const float* y0 = fr[0] >= 0 ? row(fr[0]) : nullptr;
+        const float* y1 = fr[1] >= 0 ? row(fr[1]) : nullptr;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const int j = P::node(NG - 1, t, k);
@@ -274,17 +313,20 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
         const int frame = fr[h];
         uint32_t* pb = pbits + h * (N / 32);
         for (int i = t; i < N / 32; i += T) pb[i] = 0u;
-        frame_sync<T>(slot);
+        group_sync<T, SHARED_CTA>(slot);
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const int j = P::node(0, t, k);
             const int pos = C.paypos[j];
             if (pos >= 0 && MT::neg(fadd(Lc[1][k], Rc[1][k]), h)) atomicOr(&pb[pos >> 5], 1u << (pos & 31));
         }
-        frame_sync<T>(slot);
+        group_sync<T, SHARED_CTA>(slot);
+        // the packed payload has ceil(P/8) <= N/8 bytes; a wider output row (a mixed batch uses
+        // the widest code's row) is zero-filled beyond it
         const uint8_t* pbb = reinterpret_cast<const uint8_t*>(pb);
         uint8_t* out = a.bits + (size_t)frame * a.row_bytes;
-        for (int i = t; i < a.row_bytes; i += T) out[i] = pbb[i];
+        const int prow = (C.P + 7) >> 3;
+        for (int i = t; i < a.row_bytes; i += T) out[i] = i < prow ? pbb[i] : (uint8_t)0;
         if (t == 0) {
             a.iters[frame] = (uint16_t)it_done;
             a.status[frame] = ok ? POLAR_FRAME_BP_OK : POLAR_FRAME_BP_FAIL;
@@ -325,7 +367,7 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
     auto refill = [&](int h) {
         fr[h] = fetch();
         itc[h] = 0;
-        const float* y = fr[h] >= 0 ? a.llr + (size_t)fr[h] * N : nullptr;
+        const float* y = fr[h] >= 0 ? row(fr[h]) : nullptr;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const float v = y ? stage_clip(__ldg(y + P::node(NG - 1, t, k)), M) : 0.0f;
@@ -371,7 +413,7 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
                 }
             }
             if constexpr (cross) {
-                frame_sync<T>(slot);
+                group_sync<T, SHARED_CTA>(slot);
 #pragma unroll
                 for (int k = 0; k < R; ++k) Rc[s + 1][k] = xb[P::swz(P::node(P::grp(s), t, k))];
             }
@@ -404,7 +446,7 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
                 }
             }
             if constexpr (cross) {
-                frame_sync<T>(slot);
+                group_sync<T, SHARED_CTA>(slot);
 #pragma unroll
                 for (int k = 0; k < R; ++k) Lc[s][k] = xb[P::swz(P::node(P::grp(s - 2), t, k))];
             }
@@ -429,7 +471,7 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
                 sp[t >> 5] = syn0;
                 if constexpr (FPT == 2) sp[NW + (t >> 5)] = syn1;
             }
-            frame_sync<T>(slot);
+            group_sync<T, SHARED_CTA>(slot);
             syn0 = 0;
             syn1 = 0;
 #pragma unroll
@@ -454,6 +496,23 @@ __global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
         }
         if (!any) break;
     }
+}
+
+// Per-length kernel: F frame groups per CTA; THREADS = F * T (passed explicitly: launch bounds
+// take no dependent member expression).
+template <int LOGN, class MSG, bool WEIGHTED, int THREADS>
+__global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
+{
+    using P = typename BPConfig<LOGN>::Plan;
+    constexpr int F = BPConfig<LOGN>::F;
+    static_assert(THREADS == F * P::T, "launch shape");
+    static_assert(P::T <= 32 || F == 1, "frame groups wider than a warp own their CTA");
+    extern __shared__ uint32_t smem[];
+    const int slot = threadIdx.x / P::T;
+    const int t = threadIdx.x % P::T;
+    constexpr int FPT = MsgTraits<MSG>::FPT;
+    CounterSource src{a.next, a.B, (int)((blockIdx.x * F + slot) * FPT), FPT};
+    bp_run_group<P, MSG, WEIGHTED, false>(a, *a.code, slot, t, smem + slot * bp_slot_words<P>(), src);
 }
 
 }  // namespace polar

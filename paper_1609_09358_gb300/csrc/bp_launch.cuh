@@ -1,0 +1,41 @@
+// bp_launch.cuh -- per-length BP kernel selection, compiled once per message type
+// (bp_launch_fp32.cu, bp_launch_fp16.cu).
+#pragma once
+
+#include "bp_kernel.cuh"
+
+namespace polar {
+
+struct BPKernelInfo {
+    const void* fn;
+    int threads;
+    size_t smem;
+    int groups_per_cta;  // frame groups (frames, or frame pairs for half2) per CTA
+};
+
+// kernel of (log2 N, weighted) for the message type of this translation unit
+BPKernelInfo bp_kernel_info_fp32(int logn, bool weighted);
+BPKernelInfo bp_kernel_info_fp16(int logn, bool weighted);
+
+template <class MSG>
+BPKernelInfo bp_kernel_info_t(int logn, bool weighted)
+{
+    auto pick = [&](auto LOGN_C) -> BPKernelInfo {
+        constexpr int LOGN = decltype(LOGN_C)::value;
+        using Cfg = BPConfig<LOGN>;
+        using P = typename Cfg::Plan;
+        constexpr int TH = Cfg::F * P::T;
+        const size_t smem = (size_t)Cfg::F * bp_slot_words<P>() * 4;
+        const void* fn = weighted ? (const void*)bp_kernel<LOGN, MSG, true, TH> : (const void*)bp_kernel<LOGN, MSG, false, TH>;
+        return {fn, TH, smem, Cfg::F};
+    };
+    switch (logn) {
+        case 7: return pick(std::integral_constant<int, 7>{});
+        case 8: return pick(std::integral_constant<int, 8>{});
+        case 9: return pick(std::integral_constant<int, 9>{});
+        case 10: return pick(std::integral_constant<int, 10>{});
+        default: return pick(std::integral_constant<int, 11>{});
+    }
+}
+
+}  // namespace polar

@@ -1,0 +1,23 @@
+// mixed_launch.cu -- translation unit of the mixed-batch BP kernel and the bucketing kernels
+// (see mixed_kernels.cuh).
+#define POLAR_MIXED_KERNELS
+#include "mixed_kernels.cuh"
+
+namespace polar {
+
+const void* bp_mixed_fn(int precision)
+{
+    return precision == POLAR_FP16 ? (const void*)bp_mixed_kernel<__half2> : (const void*)bp_mixed_kernel<float>;
+}
+
+cudaError_t mix_bucketing(const int* code_of, int B, int ncodes, int* counts, int* start, int* cursor, int* order,
+                          cudaStream_t st)
+{
+    const int tb = 256, nb = (B + tb - 1) / tb;
+    mix_count_kernel<<<nb, tb, 0, st>>>(code_of, B, ncodes, counts);
+    mix_scan_kernel<<<1, 1, 0, st>>>(counts, ncodes, start, cursor);
+    mix_scatter_kernel<<<nb, tb, 0, st>>>(code_of, B, ncodes, cursor, order);
+    return cudaGetLastError();
+}
+
+}  // namespace polar

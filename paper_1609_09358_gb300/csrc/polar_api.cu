@@ -10,9 +10,10 @@
 #include <string>
 #include <vector>
 
-#include "bp_kernel.cuh"
+#include "bp_launch.cuh"
 #include "encode_kernels.cuh"
 #include "polar_common.cuh"
+#include "mixed_kernels.cuh"
 #include "scl_kernel.cuh"
 #include "wms_kernels.cuh"
 
@@ -308,39 +309,24 @@ static int launch_bp(const DevCode* dcode, const polar_code* code, const float* 
     a.fail_list = fail_list;
     a.row_bytes = (code->K - code->crc_len + 7) / 8;
     const int n = log2i(code->N);
-    auto go = [&](auto LOGN_C) -> int {
-        constexpr int LOGN = decltype(LOGN_C)::value;
-        using Cfg = BPConfig<LOGN>;
-        using P = typename Cfg::Plan;
-        const int fpt = precision == POLAR_FP16 ? 2 : 1;
-        const int groups = (B + fpt - 1) / fpt;
-        int grid = (groups + Cfg::F - 1) / Cfg::F;
-        const size_t smem = (size_t)Cfg::F * bp_slot_words<P>() * 4;
-        constexpr int TH = Cfg::F * P::T;
-        const void* fn = precision == POLAR_FP16
-                             ? (w ? (const void*)bp_kernel<LOGN, __half2, true, TH> : (const void*)bp_kernel<LOGN, __half2, false, TH>)
-                             : (w ? (const void*)bp_kernel<LOGN, float, true, TH> : (const void*)bp_kernel<LOGN, float, false, TH>);
-        if (next) {
-            // persistent: as many CTAs as are resident at once; groups refill from the counter
-            int per_sm = 0, sms = scl_sm_count();
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TH, smem);
-            if (e != cudaSuccess) return cuda_fail(e, "bp occupancy");
-            grid = std::min(grid, std::max(1, per_sm) * sms);
-        }
-        void* args[] = {&a};
-        cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(TH), args, smem, stream);
-        return e == cudaSuccess ? POLAR_OK : cuda_fail(e, "bp_kernel launch");
-    };
     if (B == 0) return POLAR_OK;
-    ProfScope prof(0, stream);
-    switch (n) {
-        case 7: return go(std::integral_constant<int, 7>{});
-        case 8: return go(std::integral_constant<int, 8>{});
-        case 9: return go(std::integral_constant<int, 9>{});
-        case 10: return go(std::integral_constant<int, 10>{});
-        case 11: return go(std::integral_constant<int, 11>{});
-        default: return fail(POLAR_ERR_ARG, "unsupported N = %d", code->N);
+    if (n < 7 || n > 11) return fail(POLAR_ERR_ARG, "unsupported N = %d", code->N);
+    const BPKernelInfo k = precision == POLAR_FP16 ? bp_kernel_info_fp16(n, w != nullptr) : bp_kernel_info_fp32(n, w != nullptr);
+    const int fpt = precision == POLAR_FP16 ? 2 : 1;
+    const int groups = (B + fpt - 1) / fpt;
+    const int F = k.groups_per_cta;
+    int grid = (groups + F - 1) / F;
+    if (next) {
+        // persistent: as many CTAs as are resident at once; groups refill from the counter
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.threads, k.smem);
+        if (e != cudaSuccess) return cuda_fail(e, "bp occupancy");
+        grid = std::min(grid, std::max(1, per_sm) * scl_sm_count());
     }
+    ProfScope prof(0, stream);
+    void* args[] = {&a};
+    const cudaError_t e = cudaLaunchKernel(k.fn, dim3(grid), dim3(k.threads), args, k.smem, stream);
+    return e == cudaSuccess ? POLAR_OK : cuda_fail(e, "bp_kernel launch");
 }
 
 static int check_bp_args(const polar_code* code, const float* llr, int B, int max_iters, float llr_max,
@@ -668,6 +654,250 @@ int wms_backward(const polar_code* code, const float* llr, int32_t B, int32_t T,
     a.grad_w = grad_w;
     wms_backward_kernel<<<B, code->N / 2, 0, st>>>(a);
     POLAR_CUDA(cudaGetLastError());
+    return POLAR_OK;
+}
+
+// ------------------------------------------------------------------------------ mixed batches
+namespace {
+
+struct MixLayout {
+    size_t counts, start, cursor, qnext, order, list, scratch, total;
+};
+MixLayout mix_layout(int ncodes, int B, size_t scratch_bytes)
+{
+    MixLayout m{};
+    size_t o = kHeaderBytes;
+    m.counts = o;
+    o += sizeof(int) * ncodes;
+    m.start = o;
+    o += sizeof(int) * (ncodes + 1);
+    m.cursor = o;
+    o += sizeof(int) * ncodes;
+    m.qnext = o;
+    o += sizeof(int) * ncodes;
+    o = align_up(o, 256);
+    m.order = o;
+    o = align_up(o + sizeof(int) * (size_t)std::max(B, 1), 256);
+    m.list = o;
+    o = align_up(o + sizeof(int) * (size_t)std::max(B, 1), 256);
+    m.scratch = o;
+    m.total = o + scratch_bytes;
+    return m;
+}
+
+int mix_check(const polar_code* codes, int ncodes, int B, int L, int row_stride, int* max_row, int* warp_words,
+              long long* slot_words)
+{
+    if (!codes || ncodes < 1 || ncodes > POLAR_MAX_MIX_CODES)
+        return fail(POLAR_ERR_ARG, "ncodes = %d: must be in [1, %d]", ncodes, POLAR_MAX_MIX_CODES);
+    if (B < 0) return fail(POLAR_ERR_ARG, "B < 0");
+    int mr = 0, ww = 0;
+    long long sw = 0;
+    for (int c = 0; c < ncodes; ++c) {
+        int rc = check_code(&codes[c]);
+        if (rc) return rc;
+        mr = std::max(mr, (codes[c].K - codes[c].crc_len + 7) / 8);
+        if (L > 0) {
+            const SCLPlan p = scl_plan(codes[c].N, L, false);
+            ww = std::max(ww, p.warp_words);
+            sw = std::max(sw, p.slot_words);
+        }
+    }
+    if (row_stride >= 0 && row_stride < mr) return fail(POLAR_ERR_ARG, "row_stride %d < %d bytes", row_stride, mr);
+    if (max_row) *max_row = mr;
+    if (warp_words) *warp_words = ww;
+    if (slot_words) *slot_words = sw;
+    return POLAR_OK;
+}
+
+std::mutex g_mix_mutex;
+int g_mix_variant[2][12];  // [precision][log2 N] -> plan variant (0 = default)
+
+int mix_default_variant(int n, int precision)
+{
+    std::lock_guard<std::mutex> lock(g_mix_mutex);
+    const int v = g_mix_variant[precision][n];
+    if (v) return v;
+    return n == 7 ? 0 : n == 8 ? 1 : n == 9 ? 3 : n == 10 ? 5 : 6;
+}
+
+// Bucketing and the BP launch of a mixed batch (variants[c] per code); fail list into ws.
+int mix_bp(const polar_code* codes, int ncodes, const DevCode* const* dcodes, const int* variants, const int32_t* code_of,
+           const int64_t* llr_off, const float* llr, int B, int max_iters, float llr_max, int precision, uint8_t* bits,
+           int row_stride, uint8_t* status, uint16_t* iters, char* ws, const MixLayout& ml, cudaStream_t st)
+{
+    int* hdr = reinterpret_cast<int*>(ws);
+    int* counts = reinterpret_cast<int*>(ws + ml.counts);
+    int* start = reinterpret_cast<int*>(ws + ml.start);
+    int* cursor = reinterpret_cast<int*>(ws + ml.cursor);
+    int* qnext = reinterpret_cast<int*>(ws + ml.qnext);
+    int* order = reinterpret_cast<int*>(ws + ml.order);
+    int* list = reinterpret_cast<int*>(ws + ml.list);
+    POLAR_CUDA(cudaMemsetAsync(ws, 0, ml.order, st));
+    POLAR_CUDA(mix_bucketing(code_of, B, ncodes, counts, start, cursor, order, st));
+    MixedArgs m{};
+    m.base.llr = llr;
+    m.base.llr_off = reinterpret_cast<const long long*>(llr_off);
+    m.base.B = B;
+    m.base.max_iters = max_iters;
+    m.base.llr_max = llr_max;
+    m.base.bits = bits;
+    m.base.status = status;
+    m.base.iters = iters;
+    m.base.fail_count = hdr + 1;
+    m.base.fail_list = list;
+    m.base.fail_total = hdr;
+    m.base.row_bytes = row_stride;
+    m.ncodes = ncodes;
+    m.order = order;
+    m.start = start;
+    m.qnext = qnext;
+    size_t smem = 0;
+    for (int c = 0; c < ncodes; ++c) {
+        m.code[c] = dcodes[c];
+        m.variant[c] = variants[c];
+        smem = std::max(smem, mix_smem_bytes(variants[c]));
+    }
+    const void* fn = bp_mixed_fn(precision);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "bp_mixed_kernel attribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMixBlock, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "bp_mixed_kernel occupancy");
+    const int grid = std::max(1, per_sm) * scl_sm_count();
+    void* args[] = {&m};
+    ProfScope prof(0, st);
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(kMixBlock), args, smem, st);
+    return e == cudaSuccess ? POLAR_OK : cuda_fail(e, "bp_mixed_kernel launch");
+}
+
+int mix_prepare(const polar_code* codes, int ncodes, cudaStream_t st, const DevCode** dcodes)
+{
+    for (int c = 0; c < ncodes; ++c) {
+        int rc = code_slot(&codes[c], st, &dcodes[c]);
+        if (rc) return rc;
+    }
+    return POLAR_OK;
+}
+
+}  // namespace
+
+size_t polar_mixed_workspace_bytes(const polar_code* codes, int32_t ncodes, int32_t B, int32_t L)
+{
+    int mr = 0, ww = 0;
+    long long sw = 0;
+    if (!valid_L(L) || mix_check(codes, ncodes, B, L, -1, &mr, &ww, &sw) != POLAR_OK) return 0;
+    return mix_layout(ncodes, B, (size_t)scl_sm_count() * kSclWarpsPerSM * (size_t)sw * 4).total;
+}
+
+int hybrid_decode_mixed(const polar_code* codes, int32_t ncodes, const int32_t* code_of, const int64_t* llr_off,
+                        const float* llr, int32_t B, int32_t max_iters, float llr_max, int32_t precision, int32_t L,
+                        uint8_t* bits, int32_t row_stride, uint8_t* status, uint16_t* iters, void* workspace, size_t ws,
+                        void* stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int mr = 0, ww = 0;
+    long long sw = 0;
+    if (!valid_L(L)) return fail(POLAR_ERR_ARG, "L = %d: must be 1, 2, 4, 8, 16 or 32", L);
+    int rc = mix_check(codes, ncodes, B, L, row_stride, &mr, &ww, &sw);
+    if (rc) return rc;
+    if ((rc = check_bp_args(&codes[0], llr, B, max_iters, llr_max, precision, nullptr, 0, bits, status, iters))) return rc;
+    if (B > 0 && (!code_of || !llr_off || !bits)) return fail(POLAR_ERR_ARG, "NULL code_of/llr_off/bits");
+    const DevCode* dcodes[POLAR_MAX_MIX_CODES];
+    if ((rc = mix_prepare(codes, ncodes, st, dcodes))) return rc;
+    if (B == 0) return POLAR_OK;
+    const size_t scratch = (size_t)scl_sm_count() * kSclWarpsPerSM * (size_t)sw * 4;
+    const MixLayout ml = mix_layout(ncodes, B, scratch);
+    if (!workspace || ws < ml.total) return fail(POLAR_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws, ml.total);
+    int variants[POLAR_MAX_MIX_CODES];
+    for (int c = 0; c < ncodes; ++c) variants[c] = mix_default_variant(log2i(codes[c].N), precision);
+    char* base = static_cast<char*>(workspace);
+    if ((rc = mix_bp(codes, ncodes, dcodes, variants, code_of, llr_off, llr, B, max_iters, llr_max, precision, bits,
+                     row_stride, status, iters, base, ml, st)))
+        return rc;
+    int* hdr = reinterpret_cast<int*>(base);
+    SCLArgs a{};
+    a.llr = llr;
+    a.B = B;
+    a.L = L;
+    a.bits = bits;
+    a.status = status;
+    a.code = dcodes[0];
+    a.list = reinterpret_cast<int*>(base + ml.list);
+    a.count = hdr + 1;
+    a.next = hdr + 2;
+    a.scratch = reinterpret_cast<float*>(base + ml.scratch);
+    a.row_bytes = row_stride;
+    a.code_of = code_of;
+    a.llr_off = reinterpret_cast<const long long*>(llr_off);
+    for (int c = 0; c < ncodes; ++c) a.codes[c] = dcodes[c];
+    int nmax = 0;
+    for (int c = 0; c < ncodes; ++c) nmax = std::max(nmax, codes[c].N);
+    ProfScope prof(1, st);
+    const cudaError_t e = scl_launch(a, nmax, L, st, ww, sw);
+    return e == cudaSuccess ? POLAR_OK : cuda_fail(e, "scl_kernel launch (mixed)");
+}
+
+int polar_mixed_autotune(const polar_code* codes, int32_t ncodes, const int32_t* code_of, const int64_t* llr_off,
+                         const float* llr, int32_t B, int32_t max_iters, float llr_max, int32_t precision, uint8_t* bits,
+                         int32_t row_stride, uint8_t* status, uint16_t* iters, void* workspace, size_t ws, void* stream,
+                         int32_t* chosen, float* best_ms)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int mr = 0;
+    int rc = mix_check(codes, ncodes, B, 0, row_stride, &mr, nullptr, nullptr);
+    if (rc) return rc;
+    if ((rc = check_bp_args(&codes[0], llr, B, max_iters, llr_max, precision, nullptr, 0, bits, status, iters))) return rc;
+    if (B < 1 || !code_of || !llr_off || !bits) return fail(POLAR_ERR_ARG, "autotune needs a non-empty batch");
+    const DevCode* dcodes[POLAR_MAX_MIX_CODES];
+    if ((rc = mix_prepare(codes, ncodes, st, dcodes))) return rc;
+    const MixLayout ml = mix_layout(ncodes, B, 0);
+    if (!workspace || ws < ml.scratch) return fail(POLAR_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws, ml.scratch);
+    bool has8 = false, has9 = false;
+    for (int c = 0; c < ncodes; ++c) {
+        has8 |= codes[c].N == 256;
+        has9 |= codes[c].N == 512;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    POLAR_CUDA(cudaEventCreate(&e0));
+    POLAR_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_flags = 0;
+    for (int flags = 0; flags < 4; ++flags) {
+        if (((flags & 1) && !has8) || ((flags & 2) && !has9)) continue;
+        int variants[POLAR_MAX_MIX_CODES];
+        for (int c = 0; c < ncodes; ++c) {
+            const int n = log2i(codes[c].N);
+            variants[c] = n == 7 ? 0 : n == 8 ? ((flags & 1) ? 2 : 1) : n == 9 ? ((flags & 2) ? 4 : 3) : n == 10 ? 5 : 6;
+        }
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            POLAR_CUDA(cudaEventRecord(e0, st));
+            rc = mix_bp(codes, ncodes, dcodes, variants, code_of, llr_off, llr, B, max_iters, llr_max, precision, bits,
+                        row_stride, status, iters, static_cast<char*>(workspace), ml, st);
+            if (rc) break;
+            POLAR_CUDA(cudaEventRecord(e1, st));
+            POLAR_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            POLAR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) tmin = std::min(tmin, ms);  // the first run also pays the one-time setup
+        }
+        if (rc) break;
+        if (tmin < best) {
+            best = tmin;
+            best_flags = flags;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lock(g_mix_mutex);
+        g_mix_variant[precision][8] = (best_flags & 1) ? 2 : 1;
+        g_mix_variant[precision][9] = (best_flags & 2) ? 4 : 3;
+    }
+    if (chosen) *chosen = best_flags;
+    if (best_ms) *best_ms = best;
     return POLAR_OK;
 }
 

@@ -50,15 +50,19 @@ struct SCLArgs {
     int* next;         // work counter, zero before the launch
     float* scratch;    // per-warp slots of the global levels (null: all levels in shared memory)
     int row_bytes;
-    int KS, KC;        // last LLR / partial-sum level kept in shared memory
+    int KS, KC;        // last LLR / partial-sum level kept in shared memory (single code)
     int warp_words;    // shared-memory words per warp
     long long slot_words;  // global words per warp
+    // several codes in one batch: code_of[frame] selects codes[], llr_off[frame] the LLR row
+    const int* code_of;
+    const long long* llr_off;
+    const DevCode* codes[32];
 };
 
 __host__ __device__ inline int scl_cw(int k) { return k < 5 ? 1 : 1 << (k - 5); }  // words of a level-k C array
 __host__ __device__ inline int scl_cwsum(int k) { return k <= 5 ? k : 4 + (1 << (k - 5)); }  // sum of cw(q), q < k
 
-inline int log2_host(int v)
+__host__ __device__ inline int log2_host(int v)
 {
     int n = 0;
     while ((1 << n) < v) ++n;
@@ -74,7 +78,7 @@ struct SCLPlan {
 };
 __host__ __device__ inline long long scl_smem_llr_words(int KS, int L) { return KS >= 6 ? (long long)L * ((2 << KS) - 64) : 0; }
 __host__ __device__ inline long long scl_smem_c_words(int KC, int L) { return KC >= 5 ? (long long)L * (scl_cwsum(KC + 1) - 5) : 0; }
-inline SCLPlan scl_plan(int N, int L, bool all_smem)
+__host__ __device__ inline SCLPlan scl_plan(int N, int L, bool all_smem)
 {
     const int n = log2_host(N);
     SCLPlan p{};
@@ -262,6 +266,13 @@ __device__ __forceinline__ uint32_t leaf_psum(Leaf& f, uint32_t bitv)
     return v;
 }
 
+// Launches the persistent CA-SCL grid (defined in scl_launch.cu).  `a.scratch` null selects the
+// all-shared-memory layout; warp_words_max / slot_words_max widen the per-warp storage for mixed
+// batches.
+cudaError_t scl_launch(SCLArgs a, int N, int L, cudaStream_t st, int warp_words_max = 0,
+                       long long slot_words_max = 0);
+
+#ifdef POLAR_SCL_KERNELS
 // One list step at an information bit: candidates, ranks, survivors.  Lane = path in and out;
 // returns the survivor's parent lane and decided bit, updates pm/act, reports duplication.
 template <bool TWO>
@@ -320,7 +331,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
 {
     const int lane = threadIdx.x & 31;
     const int N = C.N, n = C.n, L = a.L;
-    const float* y = a.llr + (size_t)frame * N;
+    const float* y = a.llr + (a.llr_off ? a.llr_off[frame] : (long long)frame * N);
     uint32_t pA[2] = {0u, 0u}, pC[2] = {0u, 0u};  // upper-level pointer rows of path `lane`
     float pm = 0.0f;
     int act = 1;
@@ -527,19 +538,10 @@ __global__ void __launch_bounds__(kSclWarpsPerCTA * 32) scl_kernel(const SCLArgs
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const DevCode& C = *a.code;
     const int L = a.L;
     uint32_t* ws = smem + (size_t)wid * a.warp_words;
-    SCLWarp S;
-    S.L = L;
-    S.KS = a.KS;
-    S.KC = a.KC;
-    S.sC = ws;
-    S.sA = reinterpret_cast<float*>(ws + scl_smem_c_words(a.KC, L));
     uint8_t* selc = reinterpret_cast<uint8_t*>(ws + a.warp_words - 16);
     float* slot = a.scratch ? a.scratch + ((size_t)blockIdx.x * (blockDim.x >> 5) + wid) * (size_t)a.slot_words : nullptr;
-    S.gA = slot;
-    S.gC = slot ? reinterpret_cast<uint32_t*>(slot + (size_t)L * (C.N - (2 << a.KS))) : nullptr;
     const int count = a.count ? *a.count : a.B;
     for (;;) {
         int idx = 0;
@@ -547,23 +549,38 @@ __global__ void __launch_bounds__(kSclWarpsPerCTA * 32) scl_kernel(const SCLArgs
         idx = __shfl_sync(0xffffffffu, idx, 0);
         if (idx >= count) break;
         const int frame = a.list ? a.list[idx] : idx;
+        const DevCode& C = a.code_of ? *a.codes[a.code_of[frame]] : *a.code;
+        SCLWarp S;
+        S.L = L;
+        if (a.code_of) {
+            const SCLPlan p = scl_plan(C.N, L, slot == nullptr);
+            S.KS = p.KS;
+            S.KC = p.KC;
+        } else {
+            S.KS = a.KS;
+            S.KC = a.KC;
+        }
+        S.sC = ws;
+        S.sA = reinterpret_cast<float*>(ws + scl_smem_c_words(S.KC, L));
+        S.gA = slot;
+        S.gC = slot ? reinterpret_cast<uint32_t*>(slot + (size_t)L * (C.N - (2 << S.KS))) : nullptr;
         scl_decode_frame<TWO>(a, C, frame, S, selc);
     }
 }
 
 // Persistent launch: as many CTAs as fit on the device (bounded by the global slots and, when it
-// is known on the host, by the work); returns cudaSuccess or the launch error.  `a.scratch` null
-// selects the all-shared-memory layout.
-inline cudaError_t scl_launch(SCLArgs a, int N, int L, cudaStream_t st)
+// is known on the host, by the work); returns cudaSuccess or the launch error.
+cudaError_t scl_launch(SCLArgs a, int N, int L, cudaStream_t st, int warp_words_max, long long slot_words_max)
 {
     const bool all_smem = a.scratch == nullptr;
     const SCLPlan p = scl_plan(N, L, all_smem);
     a.KS = p.KS;
     a.KC = p.KC;
-    a.warp_words = p.warp_words;
-    a.slot_words = p.slot_words;
+    a.warp_words = std::max(p.warp_words, warp_words_max);
+    a.slot_words = std::max(p.slot_words, slot_words_max);
+    const SCLPlan pw = {p.KS, p.KC, a.warp_words, a.slot_words};
     int W = kSclWarpsPerCTA;
-    const size_t wb = (size_t)p.warp_words * 4;
+    const size_t wb = (size_t)pw.warp_words * 4;
     while (W > 1 && (size_t)W * wb > 200 * 1024) W >>= 1;
     const size_t smem = (size_t)W * wb;
     const bool two = L > 16;
@@ -585,5 +602,7 @@ inline cudaError_t scl_launch(SCLArgs a, int N, int L, cudaStream_t st)
         scl_kernel<false><<<(unsigned)grid, W * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
+
+#endif  // POLAR_SCL_KERNELS
 
 }  // namespace polar

@@ -132,3 +132,80 @@ def load(path: str, device="cuda"):
 
 def sigma_of(ebn0_db: float, rate: float) -> float:
     return math.sqrt(1.0 / (2.0 * rate * 10.0 ** (ebn0_db / 10.0)))
+
+
+# ------------------------------------------------------------------------ evaluation
+def evaluate_point(code: api.PolarCode, ebn0_db: float, frames: int, variants: dict, L: int = 8, seed: int = 1609093584,
+                   device="cuda") -> dict:
+    """Hybrid decoding of the same seeded frames with each variant; variants maps a name to
+    (max_iters, precision, weights or None).  Returns FER, BER, CA-SCL fallback rate and the
+    decoding time of each."""
+    P, N = code.P, code.N
+    dev = torch.device(device)
+    payload = torch.empty((frames, code.row_bytes), dtype=torch.uint8, device=dev)
+    cw = torch.empty((frames, N // 8), dtype=torch.uint8, device=dev)
+    llr = torch.empty((frames, N), dtype=torch.float32, device=dev)
+    api.polar_random_payload(frames, P, seed, 0, payload)
+    api.polar_encode(code, payload, cw)
+    api.polar_awgn_llr(cw, N, sigma_of(ebn0_db, P / N), seed, 0, llr)
+    dec = api.Decoder(code, frames, L, device=dev)
+    out = {}
+    for name, (imax, prec, w) in variants.items():
+        M = 32.0 if prec == api.POLAR_FP16 else 20.0
+        dec.hybrid(llr, imax, M, prec, w)  # warm-up (code tables, first launch)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dec.hybrid(llr, imax, M, prec, w)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ferr = (dec.bits != payload).any(dim=1)
+        popc = torch.tensor([bin(v).count("1") for v in range(256)], dtype=torch.int64, device=dev)
+        nbit = int(popc[(dec.bits ^ payload).long()].sum().item())
+        out[name] = {"fer": float(ferr.float().mean().item()),
+                     "ber": nbit / (frames * P),
+                     "fallback_rate": float((dec.status != api.FRAME_BP_OK).float().mean().item()),
+                     "avg_bp_iters": float(dec.iters.float().mean().item()),
+                     "ms": ms, "gbit_s": P * frames / (ms * 1e-3) / 1e9}
+    return out
+
+
+def main(argv=None):
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="learned weighted min-sum BP: train / evaluate")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    tr = sub.add_parser("train")
+    tr.add_argument("--N", type=int, default=1024)
+    tr.add_argument("--K", type=int, default=512)
+    tr.add_argument("--crc", type=int, default=16)
+    tr.add_argument("--T", type=int, default=20)
+    tr.add_argument("--steps", type=int, default=400)
+    tr.add_argument("--batch", type=int, default=4096)
+    tr.add_argument("--lr", type=float, default=3e-3)
+    tr.add_argument("--out", required=True)
+    ev = sub.add_parser("eval")
+    ev.add_argument("--weights", required=True)
+    ev.add_argument("--ebn0", type=float, nargs="+", default=[1.0, 1.5, 2.0, 2.5, 3.0])
+    ev.add_argument("--frames", type=int, default=100_000)
+    ev.add_argument("--L", type=int, default=8)
+    a = ap.parse_args(argv)
+    if a.cmd == "train":
+        code = api.make_code(a.N, a.K, a.crc)
+        w, hist = train(code, T=a.T, steps=a.steps, batch=a.batch, lr=a.lr)
+        save(a.out, w, code, a.T, {"steps": a.steps, "batch": a.batch, "lr": a.lr, "ebn0_range": [1.0, 4.0],
+                                   "loss_history": hist})
+        print(json.dumps({"saved": a.out, "loss_first": hist[0][1], "loss_last": hist[-1][1]}))
+    else:
+        w, code, T, _ = load(a.weights)
+        variants = {"plain_fp32_i200": (200, api.POLAR_FP32, None), "plain_fp32_i20": (T, api.POLAR_FP32, None),
+                    "learned_fp32_i20": (T, api.POLAR_FP32, w), "learned_fp16_i20": (T, api.POLAR_FP16, w),
+                    "plain_fp16_i20": (T, api.POLAR_FP16, None)}
+        for e in a.ebn0:
+            r = evaluate_point(code, e, a.frames, variants, a.L)
+            print(json.dumps({"ebn0_db": e, "frames": a.frames, **r}), flush=True)
+
+
+if __name__ == "__main__":
+    main()
