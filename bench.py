@@ -11,6 +11,14 @@ on the device by the library's generator before timing; they (410 MB of LLRs per
 Metric: information (payload) Gbit/s = P x frames / time, summed over all ranks (weak scaling:
 every rank decodes its own frames).  `python bench.py --impl reference` times the CPU oracle on a
 bounded sample of the same workload instead.
+
+Other workloads (`--workload`, one JSON line each, same keys):
+  mixed   2^16 frames per step, N in {128..2048} x R in {1/4, 1/2, 3/4} (CRC-16) drawn per frame
+          from a seed, 2.0 dB, i_max 200, L = 8: one persistent BP launch + one CA-SCL launch
+          (autotuned plans, CUDA-graph replay); half2 FP16 (clip 32) as `value`, FP32 beside it.
+  stress  N = 2048, K = 1024 (CRC-24 0x864CFB), 1.5 dB, 1e6 frames per step in batches of 2^16:
+          learned FP16 BP (20 iterations; plain FP16 if no trained weights for this code) then
+          CA-SCL L = 32; reports the CA-SCL share of the runtime and the batch latency p50/p99.
 """
 from __future__ import annotations
 
@@ -37,9 +45,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["hybrid", "mixed", "stress"], default="hybrid")
     ap.add_argument("--precision", choices=["fp32", "fp16"], default="fp32")
     ap.add_argument("--ebn0", type=float, default=2.5)
     ap.add_argument("--frames", type=int, default=100_000)
+    ap.add_argument("--stress-frames", type=int, default=1_000_000, help="frames per step of --workload stress")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
@@ -191,7 +201,16 @@ def main():
     a = parse()
     world, rank, local = dist_setup()
     if a.impl == "reference":
+        if a.workload != "hybrid":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the oracle on the "
+                                  "default (hybrid) workload only"}))
+            return 0
         return run_reference(a, world, rank)
+    if a.workload == "mixed":
+        return run_mixed(a, world, rank, local)
+    if a.workload == "stress":
+        return run_stress(a, world, rank, local)
 
     import numpy as np
     import torch
@@ -328,9 +347,10 @@ def learned(a, llr, payload, stream, dist):
     w, lcode, T, meta = wms.load(a.weights, device=llr.device)
     B = llr.shape[0]
     dec = api.Decoder(lcode, B, LIST, device=llr.device)
+    pw = api.PreparedScales(lcode, w, api.POLAR_FP16)  # once per weight set, outside the timed loop
 
     def step():
-        dec.hybrid(llr, T, 32.0, api.POLAR_FP16, w)
+        dec.hybrid(llr, T, 32.0, api.POLAR_FP16, pw)
 
     for _ in range(max(a.warmup, 1)):
         step()
@@ -395,6 +415,251 @@ def e2e(a, code, llr, prec, llr_max, dev, stream, dist):
     value = world * code.P * B * a.steps / (float(t.item()) * 1e-3) / 1e9
     return {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": B * N * 4,
             "d2h_bytes_per_step": B * (code.row_bytes + 1 + 2), "api": "hybrid_decode_host (pinned host buffers)"}
+
+
+# ----------------------------------------------------------------------------- shared helpers
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _alu_roofline(ops: float, bp_ms: float, fp16: bool, dev) -> dict:
+    """Algorithmic lane-ops of the BP launches over their device time, against SMs x lanes x clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max_mhz = float(_peaks().get("sm_max_mhz", 2070.0))
+    lanes = 128 * (2 if fp16 else 1)
+    peak = sms * lanes * sm_max_mhz * 1e6
+    achieved = ops / (bp_ms * 1e-3) if bp_ms > 0 else 0.0
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Top/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "bp_kernel",
+            "peak_basis": "%d SMs x %d lanes x %.0f MHz (sm_max_mhz of MEASURED_PEAKS.json)" % (sms, lanes, sm_max_mhz)}
+
+
+def _timed(step, steps: int, stream, local: int, dist):
+    """Run `steps` calls of step() between CUDA events on `stream` with clock sampling: (ms, clocks)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        time.sleep(1.0)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = clk.mark()
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t1 = clk.mark()
+        time.sleep(0.3)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=torch.device("cuda", local))
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, clk.summary(t0, t1)
+
+
+def _popcount_errors(bits, payload):
+    """(frame errors [B] bool, bit error count) of packed rows over the payload bytes."""
+    import torch
+    lut = torch.tensor([bin(v).count("1") for v in range(256)], dtype=torch.int64, device=bits.device)
+    diff = (bits ^ payload).long()
+    return (diff != 0).any(dim=1), int(lut[diff].sum().item())
+
+
+# ----------------------------------------------------------------------------- mixed workload
+MIX_NS = (128, 256, 512, 1024, 2048)
+MIX_RS = (0.25, 0.5, 0.75)
+MIX_FRAMES, MIX_EBN0, MIX_IMAX, MIX_L = 1 << 16, 2.0, 200, 8
+
+
+def mixed_workload(api, torch, dev, B: int, seed: int, frame_base: int = 0):
+    """Seeded mixed batch on the device: codes, code_of, llr_off, packed LLRs, per-code payloads."""
+    import numpy as np
+    codes = [api.make_code(N, int(R * N), 16) for N in MIX_NS for R in MIX_RS]
+    rng = np.random.default_rng(seed)
+    code_of = rng.integers(0, len(codes), B).astype(np.int32)
+    sizes = np.array([codes[c].N for c in code_of], np.int64)
+    off = np.zeros(B, np.int64)
+    off[1:] = np.cumsum(sizes)[:-1]
+    llr = torch.empty(int(sizes.sum()), dtype=torch.float32, device=dev)
+    off_d = torch.from_numpy(off).to(dev)
+    payload = torch.zeros((B, max(c.row_bytes for c in codes)), dtype=torch.uint8, device=dev)
+    for c, code in enumerate(codes):
+        idx = np.nonzero(code_of == c)[0]
+        if not len(idx):
+            continue
+        nb, N, P = len(idx), code.N, code.P
+        sigma = float(np.sqrt(1.0 / (2.0 * (P / N) * 10 ** (MIX_EBN0 / 10.0))))
+        pay = torch.empty((nb, code.row_bytes), dtype=torch.uint8, device=dev)
+        cw = torch.empty((nb, N // 8), dtype=torch.uint8, device=dev)
+        l = torch.empty((nb, N), dtype=torch.float32, device=dev)
+        f0 = frame_base + (c << 32)
+        api.polar_random_payload(nb, P, seed, f0, pay)
+        api.polar_encode(code, pay, cw)
+        api.polar_awgn_llr(cw, N, sigma, seed, f0, l)
+        idx_d = torch.from_numpy(idx).to(dev)
+        llr[(off_d[idx_d].unsqueeze(1) + torch.arange(N, device=dev)).reshape(-1)] = l.reshape(-1)
+        payload[idx_d, :code.row_bytes] = pay
+    return codes, code_of, torch.from_numpy(code_of).to(dev), off_d, llr, payload
+
+
+def run_mixed(a, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1609_09358_gb300 import api, build
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    api.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    B = MIX_FRAMES
+    codes, code_of_h, code_of, off, llr, payload = mixed_workload(api, torch, dev, B, SEED + 4, frame_base=rank * B)
+    P_total = int(sum(codes[c].P for c in code_of_h))
+    steps = a.steps
+    out = {}
+    for name, prec, M in (("fp16", api.POLAR_FP16, 32.0), ("fp32", api.POLAR_FP32, LLR_MAX)):
+        dec = api.MixedDecoder(codes, B, MIX_L, device=dev)
+        chosen, _ = dec.autotune(code_of, off, llr, MIX_IMAX, M, prec)
+        # one profiled eager decode: BP / CA-SCL device time and decoding statistics
+        api.polar_profile_enable(True)
+        dec.decode(code_of, off, llr, MIX_IMAX, M, prec)
+        torch.cuda.synchronize()
+        api.polar_profile_enable(False)
+        bp_ms, bp_n, scl_ms, scl_n = api.polar_profile_read()
+        iters = dec.iters.cpu().numpy().astype(np.int64)
+        ferr, nbit = _popcount_errors(dec.bits, payload)
+        ops = float(sum((6 * codes[c].n * codes[c].N + codes[c].K) * int(it) for c, it in zip(code_of_h, iters)))
+        dec.capture(code_of, off, llr, MIX_IMAX, M, prec)
+        for _ in range(max(a.warmup, 1)):
+            dec.replay()
+        ms, clocks = _timed(dec.replay, steps, stream, local, dist)
+        out[name] = {"value": world * P_total * steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / steps,
+                     "fer": float(ferr.float().mean().item()), "ber": nbit / P_total,
+                     "fallback_rate": float((dec.status != api.FRAME_BP_OK).float().mean().item()),
+                     "avg_bp_iters": float(iters.mean()), "bp_ms": bp_ms, "scl_ms": scl_ms,
+                     "autotune_variants": chosen, "roofline": _alu_roofline(ops, bp_ms, prec == api.POLAR_FP16, dev),
+                     "clocks": clocks}
+        out[name]["roofline"]["kernel"] = "bp_mixed_kernel"
+        del dec
+    h = out["fp16"]
+    line = {"metric": METRIC + " (mixed workload)", "value": h["value"], "unit": "Gbit/s", "n_gpus": world,
+            "steps": steps, "warmup": a.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+            "config": {"workload": "mixed batch of %d frames per GPU, N in %s x R in {1/4,1/2,3/4} (CRC-16) per "
+                                   "frame, %.1f dB, i_max %d, L %d, autotuned plans, CUDA-graph replay"
+                                   % (B, list(MIX_NS), MIX_EBN0, MIX_IMAX, MIX_L),
+                       "payload_bits_per_step": P_total,
+                       "cache": "inputs larger than L2 (%.0f MB of LLRs per step), no flush" % (llr.numel() * 4 / 1e6)},
+            "fer": h["fer"], "ber": h["ber"], "fallback_rate": h["fallback_rate"], "avg_bp_iters": h["avg_bp_iters"],
+            "gpu_launches": 5 * steps, "roofline": h["roofline"], "clocks": h["clocks"],
+            "fp32": {k: v for k, v in out["fp32"].items() if k != "clocks"},
+            "fp16_detail": {k: h[k] for k in ("bp_ms", "scl_ms", "autotune_variants")}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+# ----------------------------------------------------------------------------- stress workload
+ST_N, ST_K, ST_CRC, ST_EBN0, ST_L, ST_T = 2048, 1024, 24, 1.5, 32, 20
+ST_FRAMES, ST_BATCH = 1_000_000, 1 << 16
+
+
+def run_stress(a, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1609_09358_gb300 import api, build, wms
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    api.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    wfile = os.path.join(ROOT, "paper_1609_09358_gb300", "weights", "wms_n2048_k1024_t20.pt")
+    if os.path.exists(wfile):
+        w, code, T, _ = wms.load(wfile, device=dev)
+        pw = api.PreparedScales(code, w, api.POLAR_FP16)
+        form = "learned FP16 (%s)" % os.path.relpath(wfile, ROOT)
+    else:
+        code, T, pw = api.make_code(ST_N, ST_K, ST_CRC), ST_T, None
+        form = "plain FP16 (no trained weights for this code)"
+    B, P, N = a.stress_frames, code.P, code.N
+    sigma = float(np.sqrt(1.0 / (2.0 * (P / N) * 10 ** (ST_EBN0 / 10.0))))
+    frame0 = rank * B
+    payload = torch.empty((B, code.row_bytes), dtype=torch.uint8, device=dev)
+    llr = torch.empty((B, N), dtype=torch.float32, device=dev)
+    for o in range(0, B, ST_BATCH):
+        nb = min(ST_BATCH, B - o)
+        cw = torch.empty((nb, N // 8), dtype=torch.uint8, device=dev)
+        api.polar_random_payload(nb, P, SEED + 5, frame0 + o, payload[o:o + nb])
+        api.polar_encode(code, payload[o:o + nb], cw)
+        api.polar_awgn_llr(cw, N, sigma, SEED + 5, frame0 + o, llr[o:o + nb])
+    dec = api.Decoder(code, ST_BATCH, ST_L, device=dev)
+    bits = torch.empty_like(payload)
+    status = torch.empty(B, dtype=torch.uint8, device=dev)
+    iters = torch.empty(B, dtype=torch.int16, device=dev)
+    batches = [(o, min(ST_BATCH, B - o)) for o in range(0, B, ST_BATCH)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in batches]
+
+    def step(record=False):
+        for i, (o, nb) in enumerate(batches):
+            if record:
+                ev[i][0].record(stream)
+            api.hybrid_decode(code, llr[o:o + nb], T, 32.0, api.POLAR_FP16, pw, ST_L, bits[o:o + nb],
+                              status[o:o + nb], iters[o:o + nb], dec.workspace)
+            if record:
+                ev[i][1].record(stream)
+
+    for _ in range(max(a.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    steps = max(1, a.steps)
+    api.polar_profile_enable(True)
+    lat = []
+
+    def timed_step():
+        step(record=True)
+
+    ms, clocks = _timed(timed_step, steps, stream, local, dist)
+    api.polar_profile_enable(False)
+    bp_ms, bp_n, scl_ms, scl_n = api.polar_profile_read()
+    lat = sorted(e0.elapsed_time(e1) for e0, e1 in ev)  # batches of the last step
+    ferr, nbit = _popcount_errors(bits, payload)
+    it = iters.cpu().numpy().astype(np.int64)
+    ops = float((6 * code.n * N + code.K) * it.sum()) * steps
+    line = {"metric": METRIC + " (fallback-heavy stress)", "value": world * P * B * steps / (ms * 1e-3) / 1e9,
+            "unit": "Gbit/s", "n_gpus": world, "steps": steps, "warmup": a.warmup, "ms_per_step": ms / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+            "config": {"workload": "N=%d K=%d CRC-24 %s, T=%d, then CA-SCL L=%d, %.1f dB, %d frames per step per GPU "
+                                   "in batches of %d" % (N, code.K, form, T, ST_L, ST_EBN0, B, ST_BATCH),
+                       "cache": "inputs larger than L2 (%.0f MB of LLRs per step), no flush" % (B * N * 4 / 1e6)},
+            "fer": float(ferr.float().mean().item()), "ber": nbit / (B * P),
+            "fallback_rate": float((status != api.FRAME_BP_OK).float().mean().item()), "avg_bp_iters": float(it.mean()),
+            "scl_share": scl_ms / max(bp_ms + scl_ms, 1e-9), "bp_ms_per_step": bp_ms / steps,
+            "scl_ms_per_step": scl_ms / steps,
+            "batch_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                 "max": float(lat[-1]), "batches": len(lat)},
+            "gpu_launches": bp_n + scl_n, "roofline": _alu_roofline(ops, bp_ms, True, dev), "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
 
 
 if __name__ == "__main__":

@@ -114,16 +114,15 @@ int polar_awgn_llr(const uint8_t* codeword, int32_t B, int32_t N, float sigma,
  *   llr: device float [B][N].  max_iters >= 1.  llr_max > 0.
  *   precision: POLAR_FP32 (bit-exact with a binary32 reference) or POLAR_FP16 (binary16
  *     messages, llr_max <= 32768).
- *   wms_scales: NULL, or device float [wms_iters][2][n][N] learned weights of a weighted
- *     min-sum BP: entry [t][0][s-1][i] scales the g term of the R message leaving PE stage s at
- *     node i in iteration t, entry [t][1][s-1][i] that of the L message; iterations
- *     t >= wms_iters run unweighted.
+ *   wms_scales: NULL, or the learned weights of a weighted min-sum BP as prepared by
+ *     wms_prepare for this code, wms_iters and precision (device, 16-byte aligned): each g term
+ *     is multiplied by its scale before the clip; iterations t >= wms_iters run unweighted.
  *   bits: device [B][ceil(P/8)] decided payload.  status: device [B] POLAR_FRAME_BP_OK or
  *     POLAR_FRAME_BP_FAIL.  iters: device uint16 [B], iterations run.
  *   llr_u, llr_x: NULL or device float [B][N], the final LLR(u) and LLR(x).
  *   workspace: may be NULL (polar_workspace_bytes(.., POLAR_OP_BP) is 0). */
 int bp_decode(const polar_code* code, const float* llr, int32_t B, int32_t max_iters,
-              float llr_max, int32_t precision, const float* wms_scales, int32_t wms_iters,
+              float llr_max, int32_t precision, const void* wms_scales, int32_t wms_iters,
               uint8_t* bits, uint8_t* status, uint16_t* iters, float* llr_u, float* llr_x,
               void* workspace, size_t ws_bytes, void* stream);
 
@@ -143,24 +142,42 @@ int scl_decode(const polar_code* code, const float* llr, int32_t B, int32_t L, u
  * scl_decode.  status: POLAR_FRAME_BP_OK, _SCL_OK or _SCL_CRC_FAIL; iters: BP iterations.
  *   workspace: device, >= polar_workspace_bytes(code, B, L, POLAR_OP_HYBRID) bytes. */
 int hybrid_decode(const polar_code* code, const float* llr, int32_t B, int32_t max_iters,
-                  float llr_max, int32_t precision, const float* wms_scales, int32_t wms_iters,
+                  float llr_max, int32_t precision, const void* wms_scales, int32_t wms_iters,
                   int32_t L, uint8_t* bits, uint8_t* status, uint16_t* iters, void* workspace,
                   size_t ws_bytes, void* stream);
 
+/* Learned weights for decoding (the configurations' learned variant; not in the paper).
+ * w: device float [wms_iters][2][n][N]; entry [t][0][s-1][i] scales the g term of the R message
+ * written to node i by PE stage s in iteration t, entry [t][1][s-1][i] that of the L message.
+ * wms_prepare rewrites them into the decoder's per-thread register order, in the message
+ * precision (binary16 values rounded to nearest even for POLAR_FP16), into `prepared` (device,
+ * 16-byte aligned, >= wms_prepared_bytes(code, wms_iters, precision) bytes, owned by the caller).
+ * The prepared buffer is then passed as wms_scales to bp_decode / hybrid_decode with the same
+ * code, wms_iters and precision; preparing once and decoding many batches reads each scale with
+ * one vector load per thread and stage.  wms_prepared_bytes returns 0 on invalid arguments.
+ * Errors: POLAR_ERR_ARG (invalid code, N outside [128, 2048], wms_iters < 1, NULL or misaligned
+ * pointer), POLAR_ERR_WORKSPACE (buffer too small), POLAR_ERR_CUDA. */
+size_t wms_prepared_bytes(const polar_code* code, int32_t wms_iters, int32_t precision);
+int wms_prepare(const polar_code* code, const float* w, int32_t wms_iters, int32_t precision,
+                void* prepared, size_t bytes, void* stream);
+
 /* Training of the learned weighted min-sum BP (the configurations' learned variant; not in the
  * paper).  wms_forward runs T iterations of the weighted BP of bp_decode (no early stop) and
- * writes LLR(u) = L_{.,1} + R_{.,1} of the last iteration, storing every message in the
- * workspace; wms_backward, given dLoss/dLLR(u), writes dLoss/dw for w[T][2][n][N] (overwritten,
- * summed over the batch) by a hand-written reverse sweep through the stored messages
- * (subgradients of min and clip).  Call wms_backward after wms_forward with the same llr, w and
- * workspace.  llr, w, llr_u, grad_llr_u, grad_w: device.  workspace: device, >=
- * wms_workspace_bytes(code, B, T).  1 <= T <= 1000. */
+ * writes LLR(u) = L_{.,1} + R_{.,1}, storing every message in the workspace: of the last
+ * iteration into llr_u [B][N] (all_iters = 0), or of every iteration into llr_u [T][B][N]
+ * (all_iters = 1, for a loss summed over iterations).  wms_backward, given dLoss/dLLR(u) in the
+ * same shape, writes dLoss/dw for w[T][2][n][N] (overwritten, summed over the batch) by a
+ * hand-written reverse sweep through the stored messages (subgradients of min and clip).  Call
+ * wms_backward after wms_forward with the same llr, w, all_iters and workspace.  llr, w, llr_u,
+ * grad_llr_u, grad_w: device.  workspace: device, >= wms_workspace_bytes(code, B, T).
+ * 1 <= T <= 1000. */
 size_t wms_workspace_bytes(const polar_code* code, int32_t B, int32_t T);
 int wms_forward(const polar_code* code, const float* llr, int32_t B, int32_t T, float llr_max,
-                const float* w, float* llr_u, void* workspace, size_t ws_bytes, void* stream);
+                const float* w, int32_t all_iters, float* llr_u, void* workspace, size_t ws_bytes,
+                void* stream);
 int wms_backward(const polar_code* code, const float* llr, int32_t B, int32_t T, float llr_max,
-                 const float* w, const float* grad_llr_u, float* grad_w, void* workspace,
-                 size_t ws_bytes, void* stream);
+                 const float* w, int32_t all_iters, const float* grad_llr_u, float* grad_w,
+                 void* workspace, size_t ws_bytes, void* stream);
 
 /* Mixed batch (the configurations' mixed workload; not in the paper): frames of up to
  * POLAR_MAX_MIX_CODES codes of different lengths and rates in one batch.  Frames are bucketed by
@@ -205,7 +222,7 @@ int polar_mixed_autotune(const polar_code* codes, int32_t ncodes, const int32_t*
  *   POLAR_OP_HYBRID_HOST). */
 #define POLAR_HOST_CHUNK 32768
 int hybrid_decode_host(const polar_code* code, const float* llr_host, int32_t B, int32_t max_iters,
-                       float llr_max, int32_t precision, const float* wms_scales, int32_t wms_iters,
+                       float llr_max, int32_t precision, const void* wms_scales, int32_t wms_iters,
                        int32_t L, uint8_t* bits_host, uint8_t* status_host, uint16_t* iters_host,
                        void* workspace, size_t ws_bytes, void* stream);
 
@@ -235,7 +252,7 @@ int polar_profile_read(double* bp_ms, int32_t* bp_launches, double* scl_ms, int3
  *   hybrid_decode. */
 #define POLAR_NOALLOC_MAX_FRAMES 65536
 int hybrid_decode_noalloc(const polar_code* code, const float* llr, int32_t B, int32_t max_iters,
-                          float llr_max, int32_t precision, const float* wms_scales,
+                          float llr_max, int32_t precision, const void* wms_scales,
                           int32_t wms_iters, int32_t L, uint8_t* bits, uint8_t* status,
                           uint16_t* iters, void* stream);
 

@@ -85,7 +85,8 @@ def _declare(L):
             _f32p, _c_int, _c_int, _u8p, _i32p, _c_int, _c_uint, _c_int, _c_int, _c_double, _c_int,
             _f32p, _c_int, _u8p, _u8p, _i32p, _f32p, _f32p, _f64p]
     for sfx in ("f32", "f64"):
-        getattr(L, "or_wms_grad_" + sfx).argtypes = [_f32p, _c_int, _u8p, _c_int, _c_double, _f32p, _f64p, _f64p]
+        getattr(L, "or_wms_grad_" + sfx).argtypes = [_f32p, _c_int, _u8p, _c_int, _c_double, _f32p, _f64p, _c_int,
+                                                     _f64p]
         getattr(L, "or_sc_decode_" + sfx).argtypes = [_f32p, _c_int, _u8p, _u8p]
         getattr(L, "or_sc_bit_llr_" + sfx).argtypes = [_f32p, _c_int, _u8p, _c_int]
         getattr(L, "or_sc_bit_llr_" + sfx).restype = _c_double
@@ -263,17 +264,22 @@ def bp_decode(llr, code: Code, max_iters: int, llr_max: float, precision: str = 
     return {"u_hat": u, "status": st, "iters": it, "llr_u": lu, "llr_x": lx, "llr_u_f64": lud}
 
 
-def wms_grad(llr, code: Code, T: int, llr_max: float, w, dy, precision: str = "f64") -> np.ndarray:
-    """d/dw of sum_b sum_i dy[b][i] LLR(u_i) after T weighted BP iterations (no early stop)."""
+def wms_grad(llr, code: Code, T: int, llr_max: float, w, dy, precision: str = "f64",
+             all_iters: bool = False) -> np.ndarray:
+    """d/dw of sum_b sum_i dy[b][i] LLR(u_i) after T weighted BP iterations (no early stop); with
+    all_iters, dy is [T][B][N] and the loss sums over the LLR(u) of every iteration."""
     llr = _f32(llr).reshape(-1, code.N)
-    dy = np.ascontiguousarray(dy, dtype=np.float64).reshape(llr.shape)
+    B = llr.shape[0]
+    dy = np.asarray(dy, dtype=np.float64)
+    dy = dy.reshape(T, B, code.N) if all_iters else dy.reshape(1, B, code.N)
     w = _f32(w)
     g = np.zeros(w.shape, np.float64)
     fn = getattr(lib(), "or_wms_grad_" + precision)
-    for b in range(llr.shape[0]):
+    for b in range(B):
         row = np.ascontiguousarray(llr[b])
-        fn(_p(row, _f32p), code.N, _p(code.frozen, _u8p), T, llr_max, _p(w, _f32p), _p(np.ascontiguousarray(dy[b]), _f64p),
-           _p(g, _f64p))
+        dyb = np.ascontiguousarray(dy[:, b, :])
+        fn(_p(row, _f32p), code.N, _p(code.frozen, _u8p), T, llr_max, _p(w, _f32p), _p(dyb, _f64p),
+           1 if all_iters else 0, _p(g, _f64p))
     return g
 
 

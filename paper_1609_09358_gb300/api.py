@@ -43,9 +43,11 @@ SIGNATURES = {
     "polar_encode": (ctypes.c_int, [_CP, _vp, _i32, _vp, _vp]),
     "polar_random_payload": (ctypes.c_int, [_i32, _i32, _u64, _u64, _vp, _vp]),
     "polar_awgn_llr": (ctypes.c_int, [_vp, _i32, _i32, _f32, _vp, _u64, _u64, _vp, _vp]),
+    "wms_prepared_bytes": (_sz, [_CP, _i32, _i32]),
+    "wms_prepare": (ctypes.c_int, [_CP, _vp, _i32, _i32, _vp, _sz, _vp]),
     "wms_workspace_bytes": (_sz, [_CP, _i32, _i32]),
-    "wms_forward": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _vp, _vp, _vp, _sz, _vp]),
-    "wms_backward": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "wms_forward": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _vp, _i32, _vp, _vp, _sz, _vp]),
+    "wms_backward": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
     "bp_decode": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
                                  _vp]),
     "scl_decode": (ctypes.c_int, [_CP, _vp, _i32, _i32, _vp, _vp, _vp, _sz, _vp]),
@@ -179,31 +181,84 @@ def wms_workspace_bytes(code: PolarCode, B: int, T: int) -> int:
     return int(load().wms_workspace_bytes(code.ref(), B, T))
 
 
+def _wms_all_iters(llr_u, B: int, T: int, N: int) -> int:
+    """1 when llr_u (or its gradient) holds every iteration [T][B][N], 0 for the last [B][N]."""
+    shape = tuple(llr_u.shape)
+    if shape == (T, B, N):
+        return 1
+    if shape == (B, N):
+        return 0
+    raise PolarError("LLR(u) tensor of shape %s: expected [B][N] or [T][B][N]" % (shape,))
+
+
 def wms_forward(code: PolarCode, llr, T: int, llr_max: float, w, llr_u, workspace, stream=None) -> None:
+    """llr_u [B][N]: LLR(u) of the last iteration; [T][B][N]: of every iteration."""
     B = llr.shape[0]
     ws_b = workspace.numel() * workspace.element_size()
-    _check(load().wms_forward(code.ref(), _ptr(llr), B, T, llr_max, _ptr(w), _ptr(llr_u), _ptr(workspace), ws_b,
-                              _stream(stream)), "wms_forward")
+    all_iters = _wms_all_iters(llr_u, B, T, code.N)
+    _check(load().wms_forward(code.ref(), _ptr(llr), B, T, llr_max, _ptr(w), all_iters, _ptr(llr_u), _ptr(workspace),
+                              ws_b, _stream(stream)), "wms_forward")
 
 
 def wms_backward(code: PolarCode, llr, T: int, llr_max: float, w, grad_llr_u, grad_w, workspace,
                  stream=None) -> None:
     B = llr.shape[0]
     ws_b = workspace.numel() * workspace.element_size()
-    _check(load().wms_backward(code.ref(), _ptr(llr), B, T, llr_max, _ptr(w), _ptr(grad_llr_u), _ptr(grad_w),
-                               _ptr(workspace), ws_b, _stream(stream)), "wms_backward")
+    all_iters = _wms_all_iters(grad_llr_u, B, T, code.N)
+    _check(load().wms_backward(code.ref(), _ptr(llr), B, T, llr_max, _ptr(w), all_iters, _ptr(grad_llr_u),
+                               _ptr(grad_w), _ptr(workspace), ws_b, _stream(stream)), "wms_backward")
 
 
 def polar_workspace_bytes(code: PolarCode, B: int, L: int, op: int) -> int:
     return int(load().polar_workspace_bytes(code.ref(), B, L, op))
 
 
+def wms_prepared_bytes(code: PolarCode, wms_iters: int, precision: int) -> int:
+    return int(load().wms_prepared_bytes(code.ref(), wms_iters, precision))
+
+
+def wms_prepare(code: PolarCode, w, precision: int, prepared, stream=None) -> None:
+    """w: CUDA float32 [T][2][n][N] -> `prepared` (CUDA uint8 tensor of wms_prepared_bytes)."""
+    nb = prepared.numel() * prepared.element_size()
+    _check(load().wms_prepare(code.ref(), _ptr(w), int(w.shape[0]), precision, _ptr(prepared), nb, _stream(stream)),
+           "wms_prepare")
+
+
+class PreparedScales:
+    """Learned weights rewritten once into the decoder's layout and precision (wms_prepare);
+    pass as `wms_scales` to the decoding calls of the same block length and precision."""
+
+    def __init__(self, code: PolarCode, w, precision: int, stream=None):
+        import torch
+        if tuple(w.shape[1:]) != (2, code.n, code.N) or w.dtype != torch.float32 or not w.is_cuda:
+            raise PolarError("weights must be a CUDA float32 tensor [T][2][n][N]")
+        self.N, self.iters, self.precision = code.N, int(w.shape[0]), precision
+        self.buf = torch.empty(wms_prepared_bytes(code, self.iters, precision), dtype=torch.uint8, device=w.device)
+        self._w = w.contiguous()  # read by the queued prepare kernel
+        wms_prepare(code, self._w, precision, self.buf, stream)
+
+
+def _scales(code: PolarCode, wms_scales, precision: int, stream):
+    """(pointer, iterations, keep-alive) of the wms_scales argument of a decoding call: None, a
+    PreparedScales of this length and precision, or natural-layout weights prepared for this call."""
+    if wms_scales is None:
+        return None, 0, None
+    if not isinstance(wms_scales, PreparedScales):
+        wms_scales = PreparedScales(code, wms_scales, precision, stream)
+        if stream is not None:
+            wms_scales.buf.record_stream(stream)
+    if wms_scales.N != code.N or wms_scales.precision != precision:
+        raise PolarError("prepared weights are for N = %d, precision %d" % (wms_scales.N, wms_scales.precision))
+    return wms_scales.buf.data_ptr(), wms_scales.iters, wms_scales
+
+
 def bp_decode(code: PolarCode, llr, max_iters: int, llr_max: float, precision: int, wms_scales, bits, status,
               iters, llr_u=None, llr_x=None, workspace=None, stream=None) -> None:
+    """wms_scales: None, PreparedScales, or CUDA float32 weights [T][2][n][N] (prepared per call)."""
     B = llr.shape[0]
-    w_iters = 0 if wms_scales is None else int(wms_scales.shape[0])
+    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision, stream)
     ws_b = 0 if workspace is None else workspace.numel() * workspace.element_size()
-    _check(load().bp_decode(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, _ptr(wms_scales), w_iters,
+    _check(load().bp_decode(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, wms_scales, w_iters,
                             _ptr(bits), _ptr(status), _ptr(iters), _ptr(llr_u), _ptr(llr_x), _ptr(workspace), ws_b,
                             _stream(stream)), "bp_decode")
 
@@ -218,9 +273,9 @@ def scl_decode(code: PolarCode, llr, L: int, bits, status, workspace, stream=Non
 def hybrid_decode(code: PolarCode, llr, max_iters: int, llr_max: float, precision: int, wms_scales, L: int, bits,
                   status, iters, workspace, stream=None) -> None:
     B = llr.shape[0]
-    w_iters = 0 if wms_scales is None else int(wms_scales.shape[0])
+    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision, stream)
     ws_b = workspace.numel() * workspace.element_size()
-    _check(load().hybrid_decode(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, _ptr(wms_scales), w_iters,
+    _check(load().hybrid_decode(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, wms_scales, w_iters,
                                 L, _ptr(bits), _ptr(status), _ptr(iters), _ptr(workspace), ws_b, _stream(stream)),
            "hybrid_decode")
 
@@ -232,10 +287,10 @@ def hybrid_decode_host(code: PolarCode, llr_host, max_iters: int, llr_max: float
     for t in (llr_host, bits_host, status_host, iters_host):
         if t.is_cuda or not t.is_contiguous():
             raise PolarError("hybrid_decode_host expects contiguous host tensors")
-    w_iters = 0 if wms_scales is None else int(wms_scales.shape[0])
+    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision, stream)
     ws_b = workspace.numel() * workspace.element_size()
     _check(load().hybrid_decode_host(code.ref(), llr_host.data_ptr(), B, max_iters, llr_max, precision,
-                                     _ptr(wms_scales), w_iters, L, bits_host.data_ptr(), status_host.data_ptr(),
+                                     wms_scales, w_iters, L, bits_host.data_ptr(), status_host.data_ptr(),
                                      iters_host.data_ptr(), _ptr(workspace), ws_b, _stream(stream)),
            "hybrid_decode_host")
 
@@ -246,8 +301,8 @@ def hybrid_decode_noalloc(code: PolarCode, llr, max_iters: int, llr_max: float, 
     library's static scratch array is used instead (B <= 65536 frames, CA-SCL list in shared
     memory).  Calls that overlap on the GPU race on that array."""
     B = llr.shape[0]
-    w_iters = 0 if wms_scales is None else int(wms_scales.shape[0])
-    _check(load().hybrid_decode_noalloc(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, _ptr(wms_scales),
+    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision, stream)
+    _check(load().hybrid_decode_noalloc(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, wms_scales,
                                         w_iters, L, _ptr(bits), _ptr(status), _ptr(iters), _stream(stream)),
            "hybrid_decode_noalloc")
 

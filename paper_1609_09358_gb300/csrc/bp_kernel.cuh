@@ -25,6 +25,7 @@
 // learned weight scales it: |g(a, b)| <= |a| <= M already.
 #pragma once
 
+#include <cstring>
 #include <type_traits>
 #include <utility>
 
@@ -104,7 +105,7 @@ struct BPArgs {
     int B;
     int max_iters;
     float llr_max;
-    const float* w;  // learned weights [w_iters][2][n][N] or null
+    const void* w;   // learned weights in the prepared layout (wms_prep_index) or null
     int w_iters;
     uint8_t* bits;
     uint8_t* status;
@@ -222,6 +223,72 @@ struct QueueSource {
     }
 };
 
+// Learned scales in the kernel's register layout ("prepared" weights).  Element (it, dir, s, t, k)
+// is the scale of the g term written to node P::node(P::grp(s-1), t, k) at stage s of sweep dir
+// (0: R, 1: L) in iteration it, stored [it][dir][s-1][t][k]: a thread reads the R scales of one
+// stage as one or two 16-byte vectors, and a warp reads contiguous memory.  Element type: float
+// for FP32 messages, binary16 (rounded to nearest even once) for half2 messages.
+template <class P>
+__host__ __device__ constexpr size_t wms_prep_index(int it, int dir, int s, int t, int k)
+{
+    return ((((size_t)it * 2 + dir) * P::LOGN + (s - 1)) * P::T + t) * P::R + k;
+}
+
+template <class E>
+__device__ __forceinline__ E wms_elem(float v);
+template <>
+__device__ __forceinline__ float wms_elem<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half wms_elem<__half>(float v) { return __float2half_rn(v); }
+
+// Natural layout w[it][dir][s-1][node] -> prepared layout; one thread per element.
+template <class P, class E>
+__global__ void wms_prepare_kernel(const float* __restrict__ w, int iters, E* __restrict__ out)
+{
+    const size_t total = (size_t)iters * 2 * P::LOGN * P::N;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int k = (int)(e % P::R);
+    const int t = (int)((e / P::R) % P::T);
+    const size_t row = e / P::N;                  // (it * 2 + dir) * n + (s - 1)
+    const int s1 = (int)(row % P::LOGN);
+    out[e] = wms_elem<E>(__ldg(w + row * P::N + P::node(P::grp(s1), t, k)));
+}
+
+// One thread's R prepared scales of one stage.
+template <class E, int R>
+struct WRow {
+    E v[R];
+};
+
+template <class E, int R>
+__device__ __forceinline__ WRow<E, R> wms_row(const E* p)
+{
+    constexpr int BYTES = R * (int)sizeof(E);
+    static_assert(BYTES == 8 || BYTES % 16 == 0, "prepared row size");
+    WRow<E, R> r;
+    if constexpr (BYTES == 8) {
+        const uint2 x = __ldg(reinterpret_cast<const uint2*>(p));
+        memcpy(r.v, &x, 8);
+    } else {
+#pragma unroll
+        for (int q = 0; q < BYTES / 16; ++q) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4*>(p) + q);
+            memcpy(reinterpret_cast<char*>(r.v) + 16 * q, &x, 16);
+        }
+    }
+    return r;
+}
+
+template <class E, int R>
+__device__ __forceinline__ WRow<E, R> wms_ones()
+{
+    WRow<E, R> r;
+#pragma unroll
+    for (int k = 0; k < R; ++k) r.v[k] = wms_elem<E>(1.0f);
+    return r;
+}
+
 template <int LOGN>
 struct BPConfig;  // thread plan and frames (or frame pairs) per CTA for each block length
 template <> struct BPConfig<7>  { using Plan = BPPlan<7, 2>;  static constexpr int F = 4; };
@@ -295,16 +362,36 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             Rc[c][k] = MT::splat(0.0f);
         }
 
-    // learned scale of iteration `it` (1 past the learned iterations: the same value as the plain
-    // update, since 1 * g = g and |g| <= M needs no clip)
-    auto wval = [&](int it, int dir, int s, int j) -> float {
-        return it < a.w_iters ? __ldg(a.w + (((size_t)it * 2 + dir) * n + (s - 1)) * N + j) : 1.0f;
+    // Learned scales: iteration `it` of half h reads its prepared rows; past the learned
+    // iterations (and for an idle half) the scale is 1, the same value as the plain update since
+    // 1 * g = g and |g| <= M needs no clip.
+    using WE = std::conditional_t<FPT == 2, __half, float>;
+    using Row = WRow<WE, R>;
+    const WE* wp = static_cast<const WE*>(a.w);
+    struct WPair {
+        Row h[FPT];
     };
-    auto weight = [&](int dir, int s, int j) -> MSG {
+    auto wload = [&](int dir, int s) -> WPair {
+        WPair r;
+#pragma unroll
+        for (int h = 0; h < FPT; ++h)
+            r.h[h] = (fr[h] >= 0 && itc[h] < a.w_iters) ? wms_row<WE, R>(wp + wms_prep_index<P>(itc[h], dir, s, t, 0))
+                                                        : wms_ones<WE, R>();
+        return r;
+    };
+    auto wk = [&](const WPair& r, int k) -> MSG {
         if constexpr (FPT == 2)
-            return MT::pair(wval(itc[0], dir, s, j), wval(itc[1], dir, s, j));
+            return __halves2half2(r.h[0].v[k], r.h[1].v[k]);
         else
-            return MT::splat(wval(itc[0], dir, s, j));
+            return r.h[0].v[k];
+    };
+    // scalar scale (LLR(x) output of one half): iteration it, stage s, register k
+    auto wscalar = [&](int it, int dir, int s, int k) -> float {
+        if (it >= a.w_iters) return 1.0f;
+        if constexpr (FPT == 2)
+            return __half2float(wp[wms_prep_index<P>(it, dir, s, t, k)]);
+        else
+            return wp[wms_prep_index<P>(it, dir, s, t, k)];
     };
 
     // write the decided payload bits, status and optional LLRs of frame half h after `it_done`
@@ -351,8 +438,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                 MSG gg = xmin(Rc[n][k], Lc[n + 1][k]);
                 if constexpr (WEIGHTED) {
                     // itc of this half was already advanced past the last iteration
-                    const MSG w1 = MT::splat(wval(it_done - 1, 0, n, P::node(g, t, k)));
-                    const MSG w2 = MT::splat(wval(it_done - 1, 0, n, P::node(g, t, k2)));
+                    const MSG w1 = MT::splat(wscalar(it_done - 1, 0, n, k));
+                    const MSG w2 = MT::splat(wscalar(it_done - 1, 0, n, k2));
                     o1 = clipm(fmul(w1, o1), Mv);
                     gg = fmul(w2, gg);
                 }
@@ -384,12 +471,16 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 
     int it = 0;  // iterations run by this group (selects the partial-syndrome slot parity)
     for (;;) {
+        // scales of the stage being computed and of the next one (loaded a stage ahead)
+        WPair wc{}, wn{};
+        if constexpr (WEIGHTED) wc = wload(0, 1);
         // ------------------------------------------------------------------ R sweep
         static_for<1, n + 1>([&](auto S) {
             constexpr int s = S.value, q = s - 1, g = P::grp(q), dd = 1 << (q - P::win(g));
             constexpr bool last = s == n;
             constexpr bool cross = P::rcross(s);
             MSG* xb = xbuf + (P::xidx_r(s) & 1) * N;
+            if constexpr (WEIGHTED) wn = last ? wload(1, n) : wload(0, s + 1);
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 if (k & dd) continue;
@@ -398,8 +489,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                 MSG o1 = xmin(a1, fadd(l2, a2));
                 MSG gg = xmin(a1, l1);
                 if constexpr (WEIGHTED) {
-                    o1 = clipm(fmul(weight(0, s, P::node(g, t, k)), o1), Mv);
-                    gg = fmul(weight(0, s, P::node(g, t, k2)), gg);
+                    o1 = clipm(fmul(wk(wc, k), o1), Mv);
+                    gg = fmul(wk(wc, k2), gg);
                 }
                 const MSG o2 = clipm(fadd(gg, a2), Mv);
                 if constexpr (!last) {
@@ -417,6 +508,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 #pragma unroll
                 for (int k = 0; k < R; ++k) Rc[s + 1][k] = xb[P::swz(P::node(P::grp(s), t, k))];
             }
+            if constexpr (WEIGHTED) wc = wn;
         });
         // ------------------------------------------------------------------ L sweep
         uint32_t syn0 = 0, syn1 = 0;
@@ -425,6 +517,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             constexpr bool first = s == 1;
             constexpr bool cross = P::lcross(s);
             MSG* xb = xbuf + (P::xidx_l(s) & 1) * N;
+            if constexpr (WEIGHTED && !first) wn = wload(1, s - 1);
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 if (k & dd) continue;
@@ -433,8 +526,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                 MSG o1 = xmin(l1, fadd(l2, a2));
                 MSG gg = xmin(a1, l1);
                 if constexpr (WEIGHTED) {
-                    o1 = clipm(fmul(weight(1, s, P::node(g, t, k)), o1), Mv);
-                    gg = fmul(weight(1, s, P::node(g, t, k2)), gg);
+                    o1 = clipm(fmul(wk(wc, k), o1), Mv);
+                    gg = fmul(wk(wc, k2), gg);
                 }
                 const MSG o2 = clipm(fadd(gg, l2), Mv);
                 if constexpr (cross) {
@@ -450,15 +543,24 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 #pragma unroll
                 for (int k = 0; k < R; ++k) Lc[s][k] = xb[P::swz(P::node(P::grp(s - 2), t, k))];
             }
+            if constexpr (WEIGHTED && !first) wc = wn;
             if constexpr (first) {
                 // hard decision of LLR(u) = L[1] + R[1]; XOR of the syndrome columns of the
-                // information nodes decided 1 (frozen nodes have column 0)
+                // information nodes decided 1 (frozen nodes have column 0).  On an information
+                // node R[1] = +0, so u is never -0 and its sign bit is exactly (u < 0): the
+                // decision is an arithmetic shift and the update one and-xor.
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
                     const MSG u = fadd(Lc[1][k], Rc[1][k]);
                     const uint32_t col = csyn[k * T + t];
-                    syn0 ^= MT::neg(u, 0) ? col : 0u;
-                    if constexpr (FPT == 2) syn1 ^= MT::neg(u, 1) ? col : 0u;
+                    uint32_t ub;
+                    memcpy(&ub, &u, 4);
+                    if constexpr (FPT == 2) {
+                        syn0 ^= col & (uint32_t)((int32_t)(ub << 16) >> 31);
+                        syn1 ^= col & (uint32_t)((int32_t)ub >> 31);
+                    } else {
+                        syn0 ^= col & (uint32_t)((int32_t)ub >> 31);
+                    }
                 }
             }
         });

@@ -16,6 +16,30 @@ struct BPKernelInfo {
 // kernel of (log2 N, weighted) for the message type of this translation unit
 BPKernelInfo bp_kernel_info_fp32(int logn, bool weighted);
 BPKernelInfo bp_kernel_info_fp16(int logn, bool weighted);
+// natural-layout learned weights [iters][2][n][N] -> the prepared layout of the length's plan
+cudaError_t wms_prepare_fp32(int logn, const float* w, int iters, void* out, cudaStream_t st);
+cudaError_t wms_prepare_fp16(int logn, const float* w, int iters, void* out, cudaStream_t st);
+
+template <class E>
+cudaError_t wms_prepare_t(int logn, const float* w, int iters, void* out, cudaStream_t st)
+{
+    auto go = [&](auto LOGN_C) -> cudaError_t {
+        constexpr int LOGN = decltype(LOGN_C)::value;
+        using P = typename BPConfig<LOGN>::Plan;
+        const size_t total = (size_t)iters * 2 * P::LOGN * P::N;
+        if (total == 0) return cudaSuccess;
+        const unsigned grid = (unsigned)((total + 255) / 256);
+        wms_prepare_kernel<P, E><<<grid, 256, 0, st>>>(w, iters, static_cast<E*>(out));
+        return cudaGetLastError();
+    };
+    switch (logn) {
+        case 7: return go(std::integral_constant<int, 7>{});
+        case 8: return go(std::integral_constant<int, 8>{});
+        case 9: return go(std::integral_constant<int, 9>{});
+        case 10: return go(std::integral_constant<int, 10>{});
+        default: return go(std::integral_constant<int, 11>{});
+    }
+}
 
 template <class MSG>
 BPKernelInfo bp_kernel_info_t(int logn, bool weighted)

@@ -286,7 +286,7 @@ struct ProfScope {
 };
 
 static int launch_bp(const DevCode* dcode, const polar_code* code, const float* llr, int B, int max_iters,
-                     float llr_max, int precision, const float* w, int w_iters, uint8_t* bits, uint8_t* status,
+                     float llr_max, int precision, const void* w, int w_iters, uint8_t* bits, uint8_t* status,
                      uint16_t* iters, float* llr_u, float* llr_x, int* fail_count, int* fail_list,
                      cudaStream_t stream, int* fail_total = nullptr, int* next = nullptr)
 {
@@ -330,7 +330,7 @@ static int launch_bp(const DevCode* dcode, const polar_code* code, const float* 
 }
 
 static int check_bp_args(const polar_code* code, const float* llr, int B, int max_iters, float llr_max,
-                         int precision, const float* w, int w_iters, const uint8_t* bits, const uint8_t* status,
+                         int precision, const void* w, int w_iters, const uint8_t* bits, const uint8_t* status,
                          const uint16_t* iters)
 {
     const int rc = check_code(code);
@@ -341,6 +341,7 @@ static int check_bp_args(const polar_code* code, const float* llr, int B, int ma
     if (precision != POLAR_FP32 && precision != POLAR_FP16) return fail(POLAR_ERR_ARG, "precision = %d", precision);
     if (precision == POLAR_FP16 && llr_max > 32768.0f) return fail(POLAR_ERR_ARG, "llr_max > 32768 with FP16 messages");
     if (w && w_iters < 1) return fail(POLAR_ERR_ARG, "wms_iters = %d with weights given", w_iters);
+    if (w && (reinterpret_cast<uintptr_t>(w) & 15u)) return fail(POLAR_ERR_ARG, "prepared weights not 16-byte aligned");
     if (B > 0 && (!llr || !status || !iters)) return fail(POLAR_ERR_ARG, "NULL llr/status/iters");
     if (B > 0 && !bits && code->K > code->crc_len) return fail(POLAR_ERR_ARG, "NULL bits");
     return POLAR_OK;
@@ -479,7 +480,7 @@ size_t polar_workspace_bytes(const polar_code* code, int32_t B, int32_t L, int32
 }
 
 int bp_decode(const polar_code* code, const float* llr, int32_t B, int32_t max_iters, float llr_max,
-              int32_t precision, const float* wms_scales, int32_t wms_iters, uint8_t* bits, uint8_t* status,
+              int32_t precision, const void* wms_scales, int32_t wms_iters, uint8_t* bits, uint8_t* status,
               uint16_t* iters, float* llr_u, float* llr_x, void* workspace, size_t ws, void* stream)
 {
     (void)workspace;
@@ -515,7 +516,7 @@ int scl_decode(const polar_code* code, const float* llr, int32_t B, int32_t L, u
 }
 
 int hybrid_decode(const polar_code* code, const float* llr, int32_t B, int32_t max_iters, float llr_max,
-                  int32_t precision, const float* wms_scales, int32_t wms_iters, int32_t L, uint8_t* bits,
+                  int32_t precision, const void* wms_scales, int32_t wms_iters, int32_t L, uint8_t* bits,
                   uint8_t* status, uint16_t* iters, void* workspace, size_t ws, void* stream)
 {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -541,7 +542,7 @@ int hybrid_decode(const polar_code* code, const float* llr, int32_t B, int32_t m
 }
 
 int hybrid_decode_host(const polar_code* code, const float* llr_host, int32_t B, int32_t max_iters, float llr_max,
-                       int32_t precision, const float* wms_scales, int32_t wms_iters, int32_t L, uint8_t* bits_host,
+                       int32_t precision, const void* wms_scales, int32_t wms_iters, int32_t L, uint8_t* bits_host,
                        uint8_t* status_host, uint16_t* iters_host, void* workspace, size_t ws, void* stream)
 {
     cudaStream_t st0 = static_cast<cudaStream_t>(stream);
@@ -591,6 +592,33 @@ int hybrid_decode_host(const polar_code* code, const float* llr_host, int32_t B,
     return rc;
 }
 
+size_t wms_prepared_bytes(const polar_code* code, int32_t wms_iters, int32_t precision)
+{
+    if (check_code(code) != POLAR_OK || wms_iters < 1) return 0;
+    if (precision != POLAR_FP32 && precision != POLAR_FP16) return 0;
+    const size_t elem = precision == POLAR_FP16 ? 2 : 4;
+    return (size_t)wms_iters * 2 * log2i(code->N) * code->N * elem;
+}
+
+int wms_prepare(const polar_code* code, const float* w, int32_t wms_iters, int32_t precision, void* prepared,
+                size_t bytes, void* stream)
+{
+    int rc = check_code(code);
+    if (rc) return rc;
+    if (wms_iters < 1) return fail(POLAR_ERR_ARG, "wms_iters = %d < 1", wms_iters);
+    if (precision != POLAR_FP32 && precision != POLAR_FP16) return fail(POLAR_ERR_ARG, "precision = %d", precision);
+    const int n = log2i(code->N);
+    if (n < 7 || n > 11) return fail(POLAR_ERR_ARG, "unsupported N = %d", code->N);
+    if (!w || !prepared) return fail(POLAR_ERR_ARG, "NULL weights or output");
+    if (reinterpret_cast<uintptr_t>(prepared) & 15u) return fail(POLAR_ERR_ARG, "output not 16-byte aligned");
+    const size_t need = wms_prepared_bytes(code, wms_iters, precision);
+    if (bytes < need) return fail(POLAR_ERR_WORKSPACE, "prepared buffer %zu < %zu bytes", bytes, need);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const cudaError_t e = precision == POLAR_FP16 ? wms_prepare_fp16(n, w, wms_iters, prepared, st)
+                                                  : wms_prepare_fp32(n, w, wms_iters, prepared, st);
+    return e == cudaSuccess ? POLAR_OK : cuda_fail(e, "wms_prepare launch");
+}
+
 size_t wms_workspace_bytes(const polar_code* code, int32_t B, int32_t T)
 {
     if (check_code(code) != POLAR_OK || B < 0 || T < 1) return 0;
@@ -624,7 +652,7 @@ static int wms_common(const polar_code* code, const float* llr, int B, int T, fl
 }
 
 int wms_forward(const polar_code* code, const float* llr, int32_t B, int32_t T, float llr_max, const float* w,
-                float* llr_u, void* workspace, size_t ws, void* stream)
+                int32_t all_iters, float* llr_u, void* workspace, size_t ws, void* stream)
 {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     WMSArgs a;
@@ -632,6 +660,7 @@ int wms_forward(const polar_code* code, const float* llr, int32_t B, int32_t T, 
     if (rc) return rc;
     if (B == 0) return POLAR_OK;
     if (!llr_u) return fail(POLAR_ERR_ARG, "NULL llr_u");
+    a.all = all_iters ? 1 : 0;
     a.llr_u = llr_u;
     wms_forward_kernel<<<B, code->N / 2, 0, st>>>(a);
     POLAR_CUDA(cudaGetLastError());
@@ -639,7 +668,8 @@ int wms_forward(const polar_code* code, const float* llr, int32_t B, int32_t T, 
 }
 
 int wms_backward(const polar_code* code, const float* llr, int32_t B, int32_t T, float llr_max, const float* w,
-                 const float* grad_llr_u, float* grad_w, void* workspace, size_t ws, void* stream)
+                 int32_t all_iters, const float* grad_llr_u, float* grad_w, void* workspace, size_t ws,
+                 void* stream)
 {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     WMSArgs a;
@@ -650,6 +680,7 @@ int wms_backward(const polar_code* code, const float* llr, int32_t B, int32_t T,
     POLAR_CUDA(cudaMemsetAsync(grad_w, 0, (size_t)T * 2 * n * N * sizeof(float), st));
     if (B == 0) return POLAR_OK;
     if (!grad_llr_u) return fail(POLAR_ERR_ARG, "NULL grad_llr_u");
+    a.all = all_iters ? 1 : 0;
     a.grad_u = grad_llr_u;
     a.grad_w = grad_w;
     wms_backward_kernel<<<B, code->N / 2, 0, st>>>(a);
@@ -977,7 +1008,7 @@ static int noalloc_scratch(void** out)
 }  // namespace polar
 
 extern "C" int hybrid_decode_noalloc(const polar_code* code, const float* llr, int32_t B, int32_t max_iters,
-                                     float llr_max, int32_t precision, const float* wms_scales, int32_t wms_iters,
+                                     float llr_max, int32_t precision, const void* wms_scales, int32_t wms_iters,
                                      int32_t L, uint8_t* bits, uint8_t* status, uint16_t* iters, void* stream)
 {
     cudaStream_t st = static_cast<cudaStream_t>(stream);

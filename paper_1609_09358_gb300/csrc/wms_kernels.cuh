@@ -7,7 +7,8 @@
 //                         R[s+1][j+d] = clip(w[t][0][s-1][j+d] g(R[s][j], L'[s+1][j]) + R[s][j+d])
 //   L sweep, PE stage s:  L[s][j]     = clip(w[t][1][s-1][j]   g(L[s+1][j], L[s+1][j+d] + R[s][j+d]))
 //                         L[s][j+d]   = clip(w[t][1][s-1][j+d] g(R[s][j], L[s+1][j]) + L[s+1][j+d])
-// (L' = previous iteration), output LLR(u) = L[1] + R[1].  Same arithmetic, operation by operation,
+// (L' = previous iteration), output LLR(u) = L[1] + R[1] of the last iteration, or of every
+// iteration (`all`: a per-iteration training loss).  Same arithmetic, operation by operation,
 // as the inference kernel with weights, so both agree bit for bit.
 //
 // Backward: reverse-mode through the unrolled iterations.  Message versions: R^t[s+1] depends on
@@ -32,8 +33,9 @@ struct WMSArgs {
     int B, T;
     float M;
     const float* w;        // [T][2][n][N]
-    float* llr_u;          // forward output [B][N]
-    const float* grad_u;   // backward input [B][N]
+    int all;               // outputs / their adjoints for every iteration ([T][B][N]) or the last ([B][N])
+    float* llr_u;          // forward output
+    const float* grad_u;   // backward input, same shape as llr_u
     float* grad_w;         // backward output [T][2][n][N], accumulated
     float* store;          // [B][2][T][n][N]
     float* adj;            // [B][3][n+2][N]
@@ -91,8 +93,11 @@ __global__ void __launch_bounds__(1024) wms_forward_kernel(const WMSArgs a)
             Lcol(t, s)[jd] = o2;
             __syncthreads();
         }
+        if (a.all || t == T - 1) {
+            float* out = a.llr_u + ((size_t)(a.all ? t : 0) * a.B + b) * N;
+            for (int i = p; i < N; i += blockDim.x) out[i] = fadd(Lcol(t, 1)[i], R1(i));
+        }
     }
-    for (int i = p; i < N; i += blockDim.x) a.llr_u[(size_t)b * N + i] = fadd(Lcol(T - 1, 1)[i], R1(i));
 }
 
 // Reverse of one PE: forward o1 = clip(w1 g(u, v + q)), o2 = clip(w2 g(r, u) + q2) in the
@@ -150,11 +155,16 @@ __global__ void __launch_bounds__(1024) wms_backward_kernel(const WMSArgs a)
     float* aLbuf[2] = {adj + (size_t)(n + 2) * N, adj + (size_t)2 * (n + 2) * N};
     for (size_t i = p; i < (size_t)3 * (n + 2) * N; i += blockDim.x) adj[i] = 0.0f;
     __syncthreads();
-    for (int i = p; i < N; i += blockDim.x) aLbuf[0][1 * N + i] = a.grad_u[(size_t)b * N + i];
-    __syncthreads();
     for (int t = T - 1; t >= 0; --t) {
         float* aL = aLbuf[(T - 1 - t) & 1];       // adjoints of L^t
         float* aLp = aLbuf[(T - t) & 1];          // adjoints of L^{t-1}
+        // LLR(u) of iteration t is L^t[1] + R[1]: its adjoint enters at column 1 (nothing else
+        // reads L[1], so the column holds no other contribution)
+        if (a.all || t == T - 1) {
+            const float* gu = a.grad_u + ((size_t)(a.all ? t : 0) * a.B + b) * N;
+            for (int i = p; i < N; i += blockDim.x) aL[1 * N + i] += gu[i];
+            __syncthreads();
+        }
         // ---- undo the L sweep: s = 1..n
         for (int s = 1; s <= n; ++s) {
             const int j = pe_node(p, s), jd = j + (1 << (s - 1));

@@ -18,13 +18,14 @@ from . import api
 
 
 class WMSFunction(torch.autograd.Function):
-    """LLR(u) [B][N] of T weighted BP iterations; gradient w.r.t. the weights [T][2][n][N]."""
+    """LLR(u) of T weighted BP iterations, [B][N] after the last iteration or [T][B][N] after every
+    iteration (all_iters); gradient w.r.t. the weights [T][2][n][N]."""
 
     @staticmethod
-    def forward(ctx, w, llr, code, T, llr_max):
+    def forward(ctx, w, llr, code, T, llr_max, all_iters=False):
         B, N = llr.shape
         ws = torch.empty(api.wms_workspace_bytes(code, B, T), dtype=torch.uint8, device=llr.device)
-        out = torch.empty((B, N), dtype=torch.float32, device=llr.device)
+        out = torch.empty((T, B, N) if all_iters else (B, N), dtype=torch.float32, device=llr.device)
         w = w.detach().contiguous()
         api.wms_forward(code, llr, T, llr_max, w, out, ws)
         ctx.save_for_backward(w, llr)
@@ -37,16 +38,17 @@ class WMSFunction(torch.autograd.Function):
         grad_w = torch.empty_like(w)
         api.wms_backward(ctx.code, llr, ctx.T, ctx.llr_max, w, grad_out.contiguous(), grad_w, ctx.ws)
         ctx.ws = None
-        return grad_w, None, None, None, None
+        return grad_w, None, None, None, None, None
 
 
-def wms_llr_u(w, llr, code: api.PolarCode, T: int, llr_max: float = 20.0):
-    return WMSFunction.apply(w, llr, code, T, llr_max)
+def wms_llr_u(w, llr, code: api.PolarCode, T: int, llr_max: float = 20.0, all_iters: bool = False):
+    return WMSFunction.apply(w, llr, code, T, llr_max, all_iters)
 
 
 def bce_loss(llr_u, u_info_sign, info_idx):
-    """Mean binary cross-entropy of the information bits: softplus(-s * LLR) with s = 1 - 2u."""
-    y = llr_u[:, info_idx]
+    """Mean binary cross-entropy of the information bits: softplus(-s * LLR) with s = 1 - 2u.
+    llr_u [B][N], or [T][B][N] for the mean over iterations (the per-iteration loss)."""
+    y = llr_u[..., info_idx]
     return torch.nn.functional.softplus(-u_info_sign * y).mean()
 
 
@@ -95,8 +97,9 @@ def polar_transform_bits(x):
 
 def train(code: api.PolarCode, T: int = 20, steps: int = 300, batch: int = 4096, lr: float = 3e-3,
           ebn0_range=(1.0, 4.0), llr_max: float = 20.0, seed: int = 1609093583, log_every: int = 50,
-          w0=None, device="cuda"):
-    """Adam on the BCE of the information bits of LLR(u) after T iterations; returns (w, history)."""
+          w0=None, device="cuda", all_iters: bool = False):
+    """Adam on the BCE of the information bits of LLR(u) after T iterations (all_iters: the mean
+    of the BCE after every iteration, which rewards early convergence); returns (w, history)."""
     torch.manual_seed(seed)
     n, N = code.n, code.N
     w = (torch.ones((T, 2, n, N), dtype=torch.float32, device=device) if w0 is None else w0.clone().to(device))
@@ -106,7 +109,7 @@ def train(code: api.PolarCode, T: int = 20, steps: int = 300, batch: int = 4096,
     hist = []
     for step in range(steps):
         llr, sign = src.next()
-        y = wms_llr_u(w, llr, code, T, llr_max)
+        y = wms_llr_u(w, llr, code, T, llr_max, all_iters)
         loss = bce_loss(y, sign, src.info)
         opt.zero_grad(set_to_none=True)
         loss.backward()
@@ -152,6 +155,8 @@ def evaluate_point(code: api.PolarCode, ebn0_db: float, frames: int, variants: d
     out = {}
     for name, (imax, prec, w) in variants.items():
         M = 32.0 if prec == api.POLAR_FP16 else 20.0
+        if w is not None:
+            w = api.PreparedScales(code, w, prec)
         dec.hybrid(llr, imax, M, prec, w)  # warm-up (code tables, first launch)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -184,6 +189,8 @@ def main(argv=None):
     tr.add_argument("--steps", type=int, default=400)
     tr.add_argument("--batch", type=int, default=4096)
     tr.add_argument("--lr", type=float, default=3e-3)
+    tr.add_argument("--all-iters", action="store_true", help="loss = mean BCE after every iteration")
+    tr.add_argument("--init", type=float, default=1.0, help="initial value of every scale")
     tr.add_argument("--out", required=True)
     ev = sub.add_parser("eval")
     ev.add_argument("--weights", required=True)
@@ -193,15 +200,18 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if a.cmd == "train":
         code = api.make_code(a.N, a.K, a.crc)
-        w, hist = train(code, T=a.T, steps=a.steps, batch=a.batch, lr=a.lr)
+        w0 = torch.full((a.T, 2, code.n, code.N), a.init, dtype=torch.float32)
+        w, hist = train(code, T=a.T, steps=a.steps, batch=a.batch, lr=a.lr, w0=w0, all_iters=a.all_iters)
         save(a.out, w, code, a.T, {"steps": a.steps, "batch": a.batch, "lr": a.lr, "ebn0_range": [1.0, 4.0],
-                                   "loss_history": hist})
+                                   "all_iters": a.all_iters, "init": a.init, "loss_history": hist})
         print(json.dumps({"saved": a.out, "loss_first": hist[0][1], "loss_last": hist[-1][1]}))
     else:
         w, code, T, _ = load(a.weights)
+        # i200 with learned weights: the learned scales in the first T iterations, plain after them
         variants = {"plain_fp32_i200": (200, api.POLAR_FP32, None), "plain_fp32_i20": (T, api.POLAR_FP32, None),
                     "learned_fp32_i20": (T, api.POLAR_FP32, w), "learned_fp16_i20": (T, api.POLAR_FP16, w),
-                    "plain_fp16_i20": (T, api.POLAR_FP16, None)}
+                    "plain_fp16_i20": (T, api.POLAR_FP16, None), "plain_fp16_i200": (200, api.POLAR_FP16, None),
+                    "learned_fp16_i200": (200, api.POLAR_FP16, w)}
         for e in a.ebn0:
             r = evaluate_point(code, e, a.frames, variants, a.L)
             print(json.dumps({"ebn0_db": e, "frames": a.frames, **r}), flush=True)

@@ -88,7 +88,8 @@ def test_bp_fp16_bit_exact_vs_binary16_emulation(N, K, crc, ebn0, B, imax):
     assert_bp_equal(got, ref, ocode)
 
 
-@pytest.mark.parametrize("N,K,crc", [(128, 64, 8), (1024, 512, 16), (512, 256, 16)])
+@pytest.mark.parametrize("N,K,crc", [(128, 64, 8), (256, 128, 16), (512, 256, 16), (1024, 512, 16),
+                                     (2048, 1024, 24)])
 @pytest.mark.parametrize("precision", ["f32", "f16"])
 def test_bp_weighted_bit_exact(N, K, crc, precision):
     ocode = fr.oracle_code(N, K, crc)
@@ -100,6 +101,39 @@ def test_bp_weighted_bit_exact(N, K, crc, precision):
     ref = oracle.bp_decode(llr, ocode, 10, M, precision, w=w)
     got = run_bp(ocode, llr, 10, M, api.POLAR_FP32 if precision == "f32" else api.POLAR_FP16, w=w)
     assert_bp_equal(got, ref, ocode)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_hybrid_prepared_weights_reused(precision):
+    """Weights prepared once (wms_prepare) and passed to two hybrid decodes of different batches:
+    each equals the oracle's weighted hybrid; iterations past the learned ones run unweighted."""
+    ocode = fr.oracle_code(256, 128, 16)
+    code = fr.api_code(ocode)
+    rng = np.random.default_rng(77)
+    T = 4
+    w = rng.uniform(0.6, 1.4, (T, 2, ocode.n, 256)).astype(np.float32)
+    prec = api.POLAR_FP32 if precision == "f32" else api.POLAR_FP16
+    M = 20.0 if precision == "f32" else 32.0
+    pw = api.PreparedScales(code, dev(w), prec)
+    for seed, B in ((41, 67), (42, 30)):
+        _, llr = fr.frames(ocode, 1.5, B, seed=seed)
+        # oracle hybrid: weighted BP in the message precision, FP32 CA-SCL on its failures
+        ref = oracle.bp_decode(llr, ocode, 12, M, precision, w=w, want_llr=False)
+        u_ref, st_ref = ref["u_hat"].copy(), ref["status"].copy()
+        failed = np.nonzero(st_ref != api.FRAME_BP_OK)[0]
+        assert 0 < len(failed) < B
+        scl = oracle.scl_decode(llr[failed], ocode, 4, "f32")
+        u_ref[failed] = scl["u_hat"]
+        st_ref[failed] = scl["status"]  # FRAME_SCL_OK / FRAME_SCL_CRC_FAIL
+        dec = api.Decoder(code, B, 4)
+        bits, status, iters = dec.hybrid(dev(llr), 12, M, prec, pw)
+        torch.cuda.synchronize()
+        assert np.array_equal(iters.cpu().numpy().astype(np.int32), ref["iters"])
+        assert np.array_equal(status.cpu().numpy(), st_ref)
+        assert np.array_equal(api.unpack_bits(bits.cpu().numpy(), ocode.P), oracle.payload_of(u_ref, ocode))
+    other = api.POLAR_FP16 if prec == api.POLAR_FP32 else api.POLAR_FP32
+    with pytest.raises(api.PolarError):
+        dec.hybrid(dev(llr), 12, M, other, pw)
 
 
 def test_bp_edge_inputs():

@@ -402,3 +402,36 @@ def test_wms_gradient_matches_central_differences(N, T):
         wp, wm = (w + h * v).astype(np.float32), (w - h * v).astype(np.float32)
         fd = f(wp) - f(wm)
         assert fd == pytest.approx(float(np.sum(g * (wp.astype(np.float64) - wm.astype(np.float64)))), rel=1e-5, abs=1e-12)
+
+
+@pytest.mark.parametrize("N,T", [(16, 3), (32, 4)])
+def test_wms_gradient_all_iterations_matches_central_differences(N, T):
+    """Per-iteration loss sum_t sum_i dy[t][i] LLR_t(u_i), LLR_t after t + 1 iterations (each a
+    separate FP64 forward of the oracle): the reverse sweep against central differences."""
+    frozen, info, _ = oracle.construct(N, N // 2, 0.0, 0.5)
+    code = oracle.Code(N, N // 2, 0, 0, frozen, info)
+    rng = np.random.default_rng(N + T)
+    llr = rng.normal(1.0, 2.0, (2, N)).astype(np.float32)
+    w = rng.uniform(0.7, 1.3, (T, 2, code.n, N)).astype(np.float32)
+    dy = rng.normal(size=(T, 2, N))
+
+    def f(ww):
+        tot = 0.0
+        for t in range(T):
+            y = oracle.bp_decode(llr, code, t + 1, 20.0, "f64", early_stop=False, w=ww, llr_u_double=True)["llr_u_f64"]
+            tot += float(np.sum(dy[t] * y))
+        return tot
+
+    g = oracle.wms_grad(llr, code, T, 20.0, w, dy, "f64", all_iters=True)
+    # early iterations get their own term: the gradient of iteration 0 differs from the
+    # last-iteration-only loss
+    g_last = oracle.wms_grad(llr, code, T, 20.0, w, dy[-1], "f64")
+    assert not np.allclose(g[0], g_last[0])
+    h = 1e-6
+    idx = np.argsort(-np.abs(g).ravel())[:6].tolist() + rng.choice(w.size, 6, replace=False).tolist()
+    for i in idx:
+        wp, wm = w.copy(), w.copy()
+        wp.flat[i] += h
+        wm.flat[i] -= h
+        fd = (f(wp) - f(wm)) / (float(wp.flat[i]) - float(wm.flat[i]))
+        assert fd == pytest.approx(g.flat[i], rel=1e-6, abs=1e-9), i

@@ -66,6 +66,31 @@ def test_wms_backward_matches_oracle_gradient():
     assert np.allclose(got, ref, rtol=1e-4, atol=1e-5 * np.abs(ref).max())
 
 
+def test_wms_all_iterations_forward_and_backward():
+    """Per-iteration outputs: iteration t's LLR(u) equals the oracle's weighted BP run for t + 1
+    iterations (bit for bit), and the backward of a loss over every iteration equals the oracle's
+    reverse sweep of the same loss."""
+    T, B = 5, 10
+    ocode, code, llr, _, w = _setup(128, 64, 8, B, T, 2.0, 6)
+    ws = torch.empty(api.wms_workspace_bytes(code, B, T), dtype=torch.uint8, device="cuda")
+    out = torch.empty((T, B, 128), dtype=torch.float32, device="cuda")
+    llr_d, w_d = torch.from_numpy(llr).cuda(), torch.from_numpy(w).cuda()
+    api.wms_forward(code, llr_d, T, 20.0, w_d, out, ws)
+    rng = np.random.default_rng(8)
+    dy = (rng.normal(size=(T, B, 128)) * (1 - ocode.frozen)).astype(np.float32)
+    gw = torch.empty_like(w_d)
+    api.wms_backward(code, llr_d, T, 20.0, w_d, torch.from_numpy(dy).cuda(), gw, ws)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for t in range(T):
+        ref = oracle.bp_decode(llr, ocode, t + 1, 20.0, "f32", early_stop=False, w=w)
+        assert np.array_equal(got[t], ref["llr_u"]), t
+    ref_g = oracle.wms_grad(llr, ocode, T, 20.0, w, dy.astype(np.float64), "f32", all_iters=True)
+    g = gw.double().cpu().numpy()
+    assert np.abs(ref_g).max() > 0
+    assert np.allclose(g, ref_g, rtol=1e-4, atol=1e-5 * np.abs(ref_g).max())
+
+
 def test_wms_autograd_matches_finite_differences():
     """The torch.autograd wrapper: per-coordinate central differences of the BCE loss through the
     FP64 oracle forward, on the coordinates with the largest gradient."""
@@ -92,8 +117,9 @@ def test_wms_autograd_matches_finite_differences():
     assert agree >= 7, agree  # a perturbation may straddle a min/clip kink
 
 
-def test_wms_training_reduces_loss():
+@pytest.mark.parametrize("all_iters", [False, True])
+def test_wms_training_reduces_loss(all_iters):
     code = fr.api_code(fr.oracle_code(128, 64, 8))
-    w, hist = wms.train(code, T=5, steps=40, batch=512, lr=1e-2, log_every=10)
+    w, hist = wms.train(code, T=5, steps=40, batch=512, lr=1e-2, log_every=10, all_iters=all_iters)
     assert hist[-1][1] < hist[0][1], hist
     assert torch.isfinite(w).all()
