@@ -215,7 +215,7 @@ def main():
     import numpy as np
     import torch
 
-    from paper_1609_09358_gb300 import api, build
+    from paper_1609_09358_gb300 import api, build, shard
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -229,7 +229,7 @@ def main():
     prec = api.POLAR_FP16 if a.precision == "fp16" else api.POLAR_FP32
     llr_max = 32.0 if prec == api.POLAR_FP16 else LLR_MAX
     sigma = float(np.sqrt(1.0 / (2.0 * (P / N) * 10 ** (a.ebn0 / 10.0))))
-    frame0 = rank * B
+    frame0, _ = shard.frame_range(rank, world, B)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     payload = torch.empty((B, code.row_bytes), dtype=torch.uint8, device=dev)
@@ -250,10 +250,12 @@ def main():
     iters = dec.iters.cpu().numpy().astype(np.int64)
     status = dec.status.cpu().numpy()
     bits = dec.bits
-    frame_err = (bits != payload).any(dim=1)
-    bit_err = int(sum(bin(int(v)).count("1") for v in (bits ^ payload)[frame_err].flatten().cpu().numpy()))
-    fer = float(frame_err.float().mean().item())
-    n_fb = int(np.sum(status != api.FRAME_BP_OK))
+    frame_err, bit_err = _popcount_errors(bits, payload)
+    # error and fallback counts of the whole job (every rank's frames)
+    tot = shard.sum_over_ranks({"frames": B, "frame_err": int(frame_err.sum().item()), "bit_err": bit_err,
+                                "fallback": int(np.sum(status != api.FRAME_BP_OK))}, dist, dev)
+    fer, n_fb = tot["frame_err"] / tot["frames"], tot["fallback"] / tot["frames"] * B
+    bit_err = tot["bit_err"] / world
 
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -276,11 +278,9 @@ def main():
     clocks = clk.summary(t_start, t_end)
     bp_ms, bp_n, scl_ms, scl_n = api.polar_profile_read()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if dist:
         dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = shard.max_over_ranks(ms, dist, dev)
     value = world * P * B * a.steps / (ms_max * 1e-3) / 1e9
 
     # roofline of the dominant kernel (BP): algorithmic lane-ops / measured average launch time
@@ -324,6 +324,7 @@ def main():
 
     if not a.no_learned and os.path.exists(a.weights):
         line["learned_fp16"] = learned(a, llr, payload, stream, dist)
+        line["learned_fp16_imax%d" % IMAX] = learned(a, llr, payload, stream, dist, IMAX)
     if not a.no_e2e:
         line["e2e"] = e2e(a, code, llr, prec, llr_max, dev, stream, dist)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -338,9 +339,10 @@ def main():
     return 0
 
 
-def learned(a, llr, payload, stream, dist):
+def learned(a, llr, payload, stream, dist, imax=None):
     """The learned/FP16 form on the same frames: half2 BP with the trained per-edge weights,
-    T = 20 iterations with CRC early stop, then CA-SCL L = 8 on the CRC failures."""
+    T = 20 iterations with CRC early stop, then CA-SCL L = 8 on the CRC failures (imax > T: the
+    learned scales in the first T iterations, plain min-sum after them)."""
     import torch
 
     from paper_1609_09358_gb300 import api, wms
@@ -349,8 +351,10 @@ def learned(a, llr, payload, stream, dist):
     dec = api.Decoder(lcode, B, LIST, device=llr.device)
     pw = api.PreparedScales(lcode, w, api.POLAR_FP16)  # once per weight set, outside the timed loop
 
+    imax = T if imax is None else imax
+
     def step():
-        dec.hybrid(llr, T, 32.0, api.POLAR_FP16, pw)
+        dec.hybrid(llr, imax, 32.0, api.POLAR_FP16, pw)
 
     for _ in range(max(a.warmup, 1)):
         step()
@@ -375,7 +379,7 @@ def learned(a, llr, payload, stream, dist):
     return {"value": world * lcode.P * B * steps / (float(t.item()) * 1e-3) / 1e9, "unit": "Gbit/s", "steps": steps,
             "ms_per_step": float(t.item()) / steps, "fer": float(ferr.float().mean().item()),
             "fallback_rate": float((dec.status != api.FRAME_BP_OK).float().mean().item()),
-            "avg_bp_iters": float(dec.iters.float().mean().item()), "i_max": T,
+            "avg_bp_iters": float(dec.iters.float().mean().item()), "i_max": imax, "learned_iters": T,
             "bp_ms_per_step": bp_ms / steps, "scl_ms_per_step": scl_ms / steps, "dtype": "f16",
             "weights": os.path.relpath(a.weights, ROOT), "training": {k: meta.get(k) for k in ("steps", "batch", "lr")}}
 
@@ -600,7 +604,7 @@ def run_stress(a, world, rank, local):
         form = "plain FP16 (no trained weights for this code)"
     B, P, N = a.stress_frames, code.P, code.N
     sigma = float(np.sqrt(1.0 / (2.0 * (P / N) * 10 ** (ST_EBN0 / 10.0))))
-    frame0 = rank * B
+    frame0 = rank * B  # the rank's frame range (shard.frame_range)
     payload = torch.empty((B, code.row_bytes), dtype=torch.uint8, device=dev)
     llr = torch.empty((B, N), dtype=torch.float32, device=dev)
     for o in range(0, B, ST_BATCH):

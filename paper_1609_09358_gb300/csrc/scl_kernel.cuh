@@ -76,6 +76,10 @@ struct SCLPlan {
     int warp_words;
     long long slot_words;
 };
+// Level 5 of every path is computed element-parallel into a staging row per path (33 words: the
+// pad makes both the warp's row-wise writes and the lanes' per-path reads bank-conflict free) and
+// then read into the path's registers.
+constexpr int kSclStage = 33;
 __host__ __device__ inline long long scl_smem_llr_words(int KS, int L) { return KS >= 6 ? (long long)L * ((2 << KS) - 64) : 0; }
 __host__ __device__ inline long long scl_smem_c_words(int KC, int L) { return KC >= 5 ? (long long)L * (scl_cwsum(KC + 1) - 5) : 0; }
 __host__ __device__ inline SCLPlan scl_plan(int N, int L, bool all_smem)
@@ -91,7 +95,8 @@ __host__ __device__ inline SCLPlan scl_plan(int N, int L, bool all_smem)
         p.KC = 4;
         while (p.KC + 1 <= n && 4 * scl_smem_c_words(p.KC + 1, L) <= 2048) ++p.KC;
     }
-    p.warp_words = (int)(scl_smem_llr_words(p.KS, L) + scl_smem_c_words(p.KC, L)) + 16;
+    // [C levels 5..KC][LLR levels 6..KS][level-5 staging, L rows of 33 words][list scratch, 16 words]
+    p.warp_words = (int)(scl_smem_llr_words(p.KS, L) + scl_smem_c_words(p.KC, L)) + L * kSclStage + 16;
     p.warp_words = (p.warp_words + 3) & ~3;
     p.slot_words = (long long)L * (N - (2 << p.KS)) + (long long)L * (scl_cwsum(n + 1) - scl_cwsum(p.KC + 1));
     return p;
@@ -145,6 +150,7 @@ __device__ __forceinline__ void scl_own(uint32_t (&w)[2], int k, int act, int L)
 __device__ __forceinline__ float scl_g(float a, float b, uint32_t v) { return v ? __fsub_rn(b, a) : __fadd_rn(b, a); }
 
 struct SCLWarp {
+    float* stage;  // shared level-5 staging rows [L][kSclStage]
     float* sA;     // shared LLR levels 6..KS
     uint32_t* sC;  // shared partial-sum levels 5..KC
     float* gA;     // global LLR levels KS+1..n-1
@@ -273,13 +279,33 @@ cudaError_t scl_launch(SCLArgs a, int N, int L, cudaStream_t st, int warp_words_
                        long long slot_words_max = 0);
 
 #ifdef POLAR_SCL_KERNELS
+#define SCL_FOR_8(M, B) M(B + 0) M(B + 1) M(B + 2) M(B + 3) M(B + 4) M(B + 5) M(B + 6) M(B + 7)
+#define SCL_FOR_32(M) SCL_FOR_8(M, 0) SCL_FOR_8(M, 8) SCL_FOR_8(M, 16) SCL_FOR_8(M, 24)
+
 // One list step at an information bit: candidates, ranks, survivors.  Lane = path in and out;
-// returns the survivor's parent lane and decided bit, updates pm/act, reports duplication.
+// returns the survivor's parent lane and decided bit, updates pm/act, reports duplication and
+// whether any survivor sits in another lane than its parent (`moved`, warp-uniform).
 template <bool TWO>
 __device__ __forceinline__ int scl_list_step(float lam, float& pm, int& act, int L, uint8_t* selc, uint32_t& bitv,
-                                             bool& dup)
+                                             bool& dup, bool& moved)
 {
     const int lane = threadIdx.x & 31;
+    if (act == L) {
+        // Full list: when every path's hard-decision child (metric pm) comes before every
+        // penalised child (pm + |lambda|), the L survivors are exactly the hard-decision children,
+        // in path order -- the same result as the ranking below, without it.  Metrics are >= +0,
+        // so their bit patterns order like their values.
+        const bool on = lane < act;
+        const uint32_t hd_max = __reduce_max_sync(0xffffffffu, on ? __float_as_uint(pm) : 0u);
+        const uint32_t pen_min =
+            __reduce_min_sync(0xffffffffu, on ? __float_as_uint(__fadd_rn(pm, fabsf(lam))) : 0xffffffffu);
+        if (hd_max < pen_min) {
+            bitv = lam < 0.0f ? 1u : 0u;
+            dup = false;
+            moved = false;
+            return lane;
+        }
+    }
     const int nc = 2 * act;
     float cm0, cm1 = 0.0f;
     {
@@ -323,6 +349,7 @@ __device__ __forceinline__ int scl_list_step(float lam, float& pm, int& act, int
     bitv = (uint32_t)(cq & 1);
     pm = lane < nact ? (cq < 32 ? m0 : m1) : 0.0f;
     act = nact;
+    moved = __any_sync(0xffffffffu, lane < nact && (cq >> 1) != lane);
     return cq >> 1;
 }
 
@@ -344,18 +371,22 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
         // ------------------------------------------------ upper levels on entering the block
         const int t = blk == 0 ? n : 5 + __ffs(blk) - 1;
         const int top = blk == 0 ? n - 1 : t;
-        for (int k = top; k >= 6; --k) {
-            if ((shA >> k) & 1u) {
+        for (int k = top; k >= 5; --k) {
+            // level 5 goes to the staging rows (indexed by path), levels >= 6 to their arrays
+            const bool stage = k == 5;
+            if (!stage && ((shA >> k) & 1u)) {
                 scl_own(pA, k, act, L);
                 shA &= ~(1u << k);
             }
             const bool use_g = blk != 0 && k == t;
             const bool from_ch = k + 1 == n;
             const int len = 1 << k;
-            float* dst = S.A(k);
+            float* dst = stage ? S.stage : S.A(k);
+            const int dstride = stage ? kSclStage : len;
             const float* srcb = from_ch ? y : S.A(k + 1);
             const uint32_t* cbk = S.Cl(k);
-            const uint32_t my_d = fld(pA, k), my_s = from_ch ? 0u : fld(pA, k + 1), my_c = fld(pC, k);
+            const uint32_t my_d = stage ? (uint32_t)lane : fld(pA, k), my_s = from_ch ? 0u : fld(pA, k + 1),
+                           my_c = fld(pC, k);
             const int cwk = scl_cw(k), total = act << k;
             // four elements per lane per round: all loads of a round are issued before any store,
             // so the L2 latency of the upper levels overlaps
@@ -385,45 +416,60 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                     const int e = e0 + 32 * q + lane;
                     if (e < total) {
                         const float r = use_g ? scl_g(va[q], vb[q], (vw[q] >> (jv[q] & 31)) & 1u) : xmin(va[q], vb[q]);
-                        dst[pdv[q] * len + jv[q]] = r;
+                        dst[pdv[q] * dstride + jv[q]] = r;
                     }
                 }
             }
             __syncwarp();
         }
-        // level 5 of every path into its lane's registers (from level 6 or the channel)
+        // level 5 of every path into its lane's registers (lanes past the list read row 0: the
+        // staging area has L rows)
         {
-            const bool use_g5 = blk != 0 && t == 5;
-            const float* src = (n == 6) ? y : S.A(6) + fld(pA, 6) * 64;
-            const uint32_t c5 = use_g5 ? S.Cl(5)[fld(pC, 5)] : 0u;
+            const float* row = S.stage + (lane < L ? lane : 0) * kSclStage;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float va = src[j], vb = src[j + 32];
-                lf.l5[j] = use_g5 ? scl_g(va, vb, (c5 >> j) & 1u) : xmin(va, vb);
-            }
+            for (int j = 0; j < 32; ++j) lf.l5[j] = row[j];
         }
-        // ------------------------------------------------ the 32 bits of the block, unrolled
+        // ------------------------------------------------ the 32 bits of the block
+        // A runtime loop: one copy of the list step serves all 32 bits, and only the per-bit leaf
+        // code (whose register indices are compile-time constants) is dispatched by the bit index.
+        // Unrolling the block with a list step inlined per bit overflowed the instruction cache.
         const uint32_t fw = C.frozen_bits[blk];
         uint32_t v5 = 0u;
-        static_for<0, 32>([&](auto RC) {
-            constexpr int r = RC.value;
-            const float lam = leaf_llr<r>(lf);
+#pragma unroll 1
+        for (int r = 0; r < 32; ++r) {
+            float lam = 0.0f;
+            switch (r) {
+#define SCL_LEAF_LLR(R) \
+    case R: lam = leaf_llr<R>(lf); break;
+                SCL_FOR_32(SCL_LEAF_LLR)
+#undef SCL_LEAF_LLR
+            }
             uint32_t bitv = 0u;
+            bool moved = false;
+            int parent = lane;
             if ((fw >> r) & 1u) {
                 if (lane < act && lam < 0.0f) pm = __fadd_rn(pm, fabsf(lam));
             } else {
                 bool dup = false;
-                const int parent = scl_list_step<TWO>(lam, pm, act, L, selc, bitv, dup);
-                leaf_inherit<r>(lf, parent);
-                pA[0] = __shfl_sync(0xffffffffu, pA[0], parent);
-                pA[1] = __shfl_sync(0xffffffffu, pA[1], parent);
-                pC[0] = __shfl_sync(0xffffffffu, pC[0], parent);
-                pC[1] = __shfl_sync(0xffffffffu, pC[1], parent);
+                parent = scl_list_step<TWO>(lam, pm, act, L, selc, bitv, dup, moved);
+                if (moved) {
+                    pA[0] = __shfl_sync(0xffffffffu, pA[0], parent);
+                    pA[1] = __shfl_sync(0xffffffffu, pA[1], parent);
+                    pC[0] = __shfl_sync(0xffffffffu, pC[0], parent);
+                    pC[1] = __shfl_sync(0xffffffffu, pC[1], parent);
+                }
                 if (dup) shA = shC = 0xffffffffu;
             }
-            const uint32_t v = leaf_psum<r>(lf, bitv);
-            if constexpr (r == 31) v5 = v;
-        });
+            switch (r) {
+#define SCL_LEAF_POST(R)                           \
+    case R:                                        \
+        if (moved) leaf_inherit<R>(lf, parent);    \
+        v5 = leaf_psum<R>(lf, bitv);               \
+        break;
+                SCL_FOR_32(SCL_LEAF_POST)
+#undef SCL_LEAF_POST
+            }
+        }
         // ------------------------------------------------ block complete: partial sums upward
         {
             const int i_last = blk * 32 + 31;
@@ -562,6 +608,7 @@ __global__ void __launch_bounds__(kSclWarpsPerCTA * 32) scl_kernel(const SCLArgs
         }
         S.sC = ws;
         S.sA = reinterpret_cast<float*>(ws + scl_smem_c_words(S.KC, L));
+        S.stage = S.sA + scl_smem_llr_words(S.KS, L);
         S.gA = slot;
         S.gC = slot ? reinterpret_cast<uint32_t*>(slot + (size_t)L * (C.N - (2 << S.KS))) : nullptr;
         scl_decode_frame<TWO>(a, C, frame, S, selc);
