@@ -39,15 +39,38 @@ struct BPPlan {
     static constexpr int N = 1 << LOGN, R = 1 << LOGR, T = N >> LOGR;
     static constexpr int NG = (LOGN + LOGR - 1) / LOGR;
     static constexpr int NW = (T + 31) / 32;
+    static constexpr int TB = LOGN - LOGR;  // thread-index bits
     // group of the PE stage with index bit q (stage s = q + 1)
     __host__ __device__ static constexpr int grp(int q) { return q / LOGR; }
     // first index bit of group g's register window (the last window is pulled down to fit)
     __host__ __device__ static constexpr int win(int g) { return (g + 1) * LOGR <= LOGN ? g * LOGR : LOGN - LOGR; }
-    // node held in register k by thread t while in group g
-    __host__ __device__ static constexpr int node(int g, int t, int k)
+
+    // Exchange-buffer addressing.  PAD plans use addr(j) = j + (j >> 5) + (j >> 10): it is
+    // additive over disjoint bit sets, so the R accesses of a thread are one per-thread base plus
+    // compile-time offsets (no address arithmetic per access), and it is bank-conflict free when
+    // in every group the 5 lane bits of the thread index land on node bits whose addresses are
+    // 1, 2, 4, 8, 16 modulo 32 in some order -- for group 1 that takes node bits 0, 1, 2, 8, 9
+    // (a search over the plans finds such bits for N >= 1024 with b = 3 only).  The other plans
+    // keep an XOR swizzle of index bits 5..7 into the bank bits (one XOR per access).
+    static constexpr bool PAD = LOGR == 3 && LOGN >= 10;
+    // node bit receiving thread-index bit q in group g: the non-window bits in ascending order,
+    // except that group 1 of a PAD plan puts lane bits 3, 4 on node bits 8, 9
+    __host__ __device__ static constexpr int tbit(int g, int q)
     {
-        return (t & ((1 << win(g)) - 1)) | (k << win(g)) | ((t >> win(g)) << (win(g) + LOGR));
+        if (PAD && g == 1)  // window 3..5: thread bits -> node bits 0 1 2 8 9 6 7 10 ...
+            return q < 3 ? q : q < 5 ? q + 5 : q < 7 ? q + 1 : q + 3;
+        return q < win(g) ? q : q + LOGR;
     }
+    // node bits from the thread index t (group g) and from the register index k
+    __host__ __device__ static constexpr int tpart(int g, int t)
+    {
+        int v = 0;
+        for (int q = 0; q < TB; ++q) v |= ((t >> q) & 1) << tbit(g, q);
+        return v;
+    }
+    __host__ __device__ static constexpr int kpart(int g, int k) { return k << win(g); }
+    // node held in register k by thread t while in group g
+    __host__ __device__ static constexpr int node(int g, int t, int k) { return tpart(g, t) | kpart(g, k); }
     // column exchanges: the R sweep leaving stage s crosses into another group, or the L sweep
     // leaving stage s does; xidx numbers the exchanges of one iteration in execution order
     __host__ __device__ static constexpr bool rcross(int s) { return s < LOGN && grp(s) != grp(s - 1); }
@@ -64,8 +87,7 @@ struct BPPlan {
         for (int i = LOGN; i > s; --i) c += lcross(i);
         return c;
     }
-    // shared-memory address of node j in the exchange buffer: XOR of index bits 5..7 into the
-    // bank bits, chosen so that every warp access of every group hits 32 distinct banks.
+    // XOR swizzle of the non-PAD plans: index bits 5..7 into the bank bits
     __host__ __device__ static constexpr int swz(int j)
     {
         if constexpr (LOGR == 3)
@@ -73,31 +95,60 @@ struct BPPlan {
         else
             return j ^ (((j >> 5) & 1) * 5) ^ (((j >> 6) & 1) * 26);
     }
+    __host__ __device__ static constexpr int addr(int j) { return PAD ? j + (j >> 5) + (j >> 10) : swz(j); }
+    // words of one exchange buffer
+    static constexpr int XW = PAD ? ((N + (N >> 5) + (N >> 10)) + 3) & ~3 : N;
 };
 
 template <class P>
 constexpr bool plan_is_conflict_free()
 {
+    // every group maps (thread, register) onto the N nodes one to one
+    for (int g = 0; g < P::NG; ++g) {
+        uint32_t seen[P::N / 32] = {};
+        for (int t = 0; t < P::T; ++t)
+            for (int k = 0; k < P::R; ++k) {
+                const int j = P::node(g, t, k);
+                if (j < 0 || j >= P::N || ((seen[j >> 5] >> (j & 31)) & 1u)) return false;
+                seen[j >> 5] |= 1u << (j & 31);
+            }
+    }
     for (int g = 0; g < P::NG; ++g)
         for (int k = 0; k < P::R; ++k)
             for (int w = 0; w < P::NW; ++w) {
-                uint32_t seen = 0;
+                uint32_t banks = 0;
                 for (int l = 0; l < 32 && w * 32 + l < P::T; ++l) {
-                    const int a = P::swz(P::node(g, w * 32 + l, k));
-                    if (a < 0 || a >= P::N) return false;
+                    const int t = w * 32 + l;
+                    const int a = P::addr(P::node(g, t, k));
+                    if (a < 0 || a >= P::XW) return false;
+                    // PAD: the address splits into the thread's base and the register's offset
+                    if (P::PAD && a != P::addr(P::tpart(g, t)) + P::addr(P::kpart(g, k))) return false;
                     const uint32_t bit = 1u << (a & 31);
-                    if (seen & bit) return false;
-                    seen |= bit;
+                    if (banks & bit) return false;
+                    banks |= bit;
                 }
             }
-    // every node owned exactly once per group
-    for (int g = 0; g < P::NG; ++g) {
-        int sum = 0;
-        for (int t = 0; t < P::T; ++t)
-            for (int k = 0; k < P::R; ++k) sum += P::node(g, t, k);
-        if (sum != P::N * (P::N - 1) / 2) return false;
-    }
     return true;
+}
+
+// Exchange-buffer access of register k of thread t in group G: the thread's base of group G
+// (xbase[G] = addr(tpart(G, t)), computed once) plus a compile-time offset for PAD plans, the
+// XOR-swizzled node index otherwise.
+template <class P, int G, class MSG>
+__device__ __forceinline__ void xput(MSG* xb, const int* xbase, int t, int k, MSG v)
+{
+    if constexpr (P::PAD)
+        xb[xbase[G] + P::addr(P::kpart(G, k))] = v;
+    else
+        xb[P::swz(P::node(G, t, k))] = v;
+}
+template <class P, int G, class MSG>
+__device__ __forceinline__ MSG xget(const MSG* xb, const int* xbase, int t, int k)
+{
+    if constexpr (P::PAD)
+        return xb[xbase[G] + P::addr(P::kpart(G, k))];
+    else
+        return xb[P::swz(P::node(G, t, k))];
 }
 
 struct BPArgs {
@@ -291,18 +342,20 @@ __device__ __forceinline__ WRow<E, R> wms_ones()
 
 template <int LOGN>
 struct BPConfig;  // thread plan and frames (or frame pairs) per CTA for each block length
-template <> struct BPConfig<7>  { using Plan = BPPlan<7, 2>;  static constexpr int F = 4; };
-template <> struct BPConfig<8>  { using Plan = BPPlan<8, 3>;  static constexpr int F = 4; };
-template <> struct BPConfig<9>  { using Plan = BPPlan<9, 3>;  static constexpr int F = 1; };
-template <> struct BPConfig<10> { using Plan = BPPlan<10, 3>; static constexpr int F = 1; };
-template <> struct BPConfig<11> { using Plan = BPPlan<11, 3>; static constexpr int F = 1; };
+// MIN_CTAS: resident CTAs per SM the register allocation of the plain kernel must allow (launch
+// bounds; the weighted kernel would spill)
+template <> struct BPConfig<7>  { using Plan = BPPlan<7, 2>;  static constexpr int F = 4, MIN_CTAS = 1; };
+template <> struct BPConfig<8>  { using Plan = BPPlan<8, 3>;  static constexpr int F = 4, MIN_CTAS = 1; };
+template <> struct BPConfig<9>  { using Plan = BPPlan<9, 3>;  static constexpr int F = 1, MIN_CTAS = 1; };
+template <> struct BPConfig<10> { using Plan = BPPlan<10, 3>; static constexpr int F = 1, MIN_CTAS = 4; };
+template <> struct BPConfig<11> { using Plan = BPPlan<11, 3>; static constexpr int F = 1, MIN_CTAS = 2; };
 
 template <class P>
 __host__ __device__ constexpr int bp_slot_words()
 {
-    // exchange buffer [2][N] | syndrome columns, thread-major [R][T] | partial syndromes
+    // exchange buffers [2][XW] | syndrome columns, thread-major [R][T] | partial syndromes
     // [2][2][NW] | packed payload bits [2][N/32] | fetched frame index [4]
-    return 2 * P::N + P::N + 4 * P::NW + 2 * (P::N / 32) + 4;
+    return 2 * P::XW + P::N + 4 * P::NW + 2 * (P::N / 32) + 4;
 }
 
 // One frame group of T threads decoding frames from `src` until it runs dry.  Group `slot` of
@@ -320,8 +373,10 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
     // every read of its previous contents
     static_assert(P::xidx_l(0) % 2 == 0, "odd number of exchanges per iteration");
 
-    MSG* xbuf = reinterpret_cast<MSG*>(slot_smem);         // [2][N]; half2 uses the first half
-    uint32_t* csyn = slot_smem + 2 * N;                    // [R][T]
+    MSG* xbuf = reinterpret_cast<MSG*>(slot_smem);         // [2][XW]
+    uint32_t* csyn = slot_smem + 2 * P::XW;                // [R][T]
+    int xbase[NG];                                         // exchange base of each group (PAD plans)
+    static_for<0, NG>([&](auto G) { xbase[G.value] = P::addr(P::tpart(G.value, t)); });
     uint32_t* synp = csyn + N;                             // [2 parity][2 frame][NW]
     uint32_t* pbits = synp + 4 * NW;                       // [2 frame][N/32]
     int* fetched = reinterpret_cast<int*>(pbits + 2 * (N / 32));
@@ -479,7 +534,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             constexpr int s = S.value, q = s - 1, g = P::grp(q), dd = 1 << (q - P::win(g));
             constexpr bool last = s == n;
             constexpr bool cross = P::rcross(s);
-            MSG* xb = xbuf + (P::xidx_r(s) & 1) * N;
+            MSG* xb = xbuf + (P::xidx_r(s) & 1) * P::XW;
             if constexpr (WEIGHTED) wn = last ? wload(1, n) : wload(0, s + 1);
 #pragma unroll
             for (int k = 0; k < R; ++k) {
@@ -495,8 +550,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                 const MSG o2 = clipm(fadd(gg, a2), Mv);
                 if constexpr (!last) {
                     if constexpr (cross) {
-                        xb[P::swz(P::node(g, t, k))] = o1;
-                        xb[P::swz(P::node(g, t, k2))] = o2;
+                        xput<P, g>(xb, xbase, t, k, o1);
+                        xput<P, g>(xb, xbase, t, k2, o2);
                     } else {
                         Rc[s + 1][k] = o1;
                         Rc[s + 1][k2] = o2;
@@ -506,7 +561,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             if constexpr (cross) {
                 group_sync<T, SHARED_CTA>(slot);
 #pragma unroll
-                for (int k = 0; k < R; ++k) Rc[s + 1][k] = xb[P::swz(P::node(P::grp(s), t, k))];
+                for (int k = 0; k < R; ++k) Rc[s + 1][k] = xget<P, P::grp(s)>(xb, xbase, t, k);
             }
             if constexpr (WEIGHTED) wc = wn;
         });
@@ -516,7 +571,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             constexpr int s = S.value, q = s - 1, g = P::grp(q), dd = 1 << (q - P::win(g));
             constexpr bool first = s == 1;
             constexpr bool cross = P::lcross(s);
-            MSG* xb = xbuf + (P::xidx_l(s) & 1) * N;
+            MSG* xb = xbuf + (P::xidx_l(s) & 1) * P::XW;
             if constexpr (WEIGHTED && !first) wn = wload(1, s - 1);
 #pragma unroll
             for (int k = 0; k < R; ++k) {
@@ -531,8 +586,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                 }
                 const MSG o2 = clipm(fadd(gg, l2), Mv);
                 if constexpr (cross) {
-                    xb[P::swz(P::node(g, t, k))] = o1;
-                    xb[P::swz(P::node(g, t, k2))] = o2;
+                    xput<P, g>(xb, xbase, t, k, o1);
+                    xput<P, g>(xb, xbase, t, k2, o2);
                 } else {
                     Lc[s][k] = o1;
                     Lc[s][k2] = o2;
@@ -541,7 +596,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             if constexpr (cross) {
                 group_sync<T, SHARED_CTA>(slot);
 #pragma unroll
-                for (int k = 0; k < R; ++k) Lc[s][k] = xb[P::swz(P::node(P::grp(s - 2), t, k))];
+                for (int k = 0; k < R; ++k) Lc[s][k] = xget<P, P::grp(s - 2)>(xb, xbase, t, k);
             }
             if constexpr (WEIGHTED && !first) wc = wn;
             if constexpr (first) {
@@ -603,7 +658,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 // Per-length kernel: F frame groups per CTA; THREADS = F * T (passed explicitly: launch bounds
 // take no dependent member expression).
 template <int LOGN, class MSG, bool WEIGHTED, int THREADS>
-__global__ void __launch_bounds__(THREADS) bp_kernel(const BPArgs a)
+__global__ void __launch_bounds__(THREADS, WEIGHTED ? 1 : BPConfig<LOGN>::MIN_CTAS) bp_kernel(const BPArgs a)
 {
     using P = typename BPConfig<LOGN>::Plan;
     constexpr int F = BPConfig<LOGN>::F;

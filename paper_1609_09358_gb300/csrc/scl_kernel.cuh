@@ -318,25 +318,61 @@ __device__ __forceinline__ int scl_list_step(float lam, float& pm, int& act, int
         const float pp = __shfl_sync(0xffffffffu, pm, 16 + (lane >> 1));
         cm1 = ((uint32_t)(lane & 1) != (uint32_t)(lp < 0.0f)) ? __fadd_rn(pp, fabsf(lp)) : pp;
     }
-    int rank0 = 0, rank1 = 0;
-    const int n0 = nc < 32 ? nc : 32;
-#pragma unroll 8
-    for (int c2 = 0; c2 < n0; ++c2) {
-        const float o = __shfl_sync(0xffffffffu, cm0, c2);
-        rank0 += (o < cm0) || (o == cm0 && c2 < lane);
-        if constexpr (TWO) rank1 += o <= cm1;  // every c2 < 32 precedes candidate lane + 32 on ties
-    }
-    if constexpr (TWO) {
-#pragma unroll 8
-        for (int c2 = 32; c2 < nc; ++c2) {
-            const float o = __shfl_sync(0xffffffffu, cm1, c2 - 32);
-            rank0 += o < cm0;
-            rank1 += (o < cm1) || (o == cm1 && c2 < lane + 32);
-        }
-    }
     const uint32_t below = (1u << lane) - 1u;
-    const uint32_t km0 = __ballot_sync(0xffffffffu, lane < nc && rank0 < L);
-    const uint32_t km1 = TWO ? __ballot_sync(0xffffffffu, lane + 32 < nc && rank1 < L) : 0u;
+    uint32_t km0, km1 = 0u;
+    if (nc <= L) {
+        // every candidate survives
+        km0 = __ballot_sync(0xffffffffu, lane < nc);
+        if constexpr (TWO) km1 = __ballot_sync(0xffffffffu, lane + 32 < nc);
+    } else if (TWO || nc > 16) {
+        // Threshold selection.  tau = the L-th smallest metric: with two candidates per lane, a
+        // bitonic sort of the first 32 ascending and of the second 32 descending, whose
+        // element-wise minimum holds the 32 smallest (the half-cleaner of a bitonic merge); with
+        // one per lane, the sorted value of lane L - 1.  The survivors are every candidate below
+        // tau and the lowest-index candidates equal to tau -- the L smallest in (metric, index)
+        // order, the same set as ranking every candidate.
+        const float inf = __int_as_float(0x7f800000);
+        float x0 = lane < nc ? cm0 : inf;
+        float x1 = (TWO && lane + 32 < nc) ? cm1 : inf;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const float o0 = __shfl_xor_sync(0xffffffffu, x0, j);
+                const bool take_min = ((lane & j) == 0) == ((lane & k) == 0);
+                if constexpr (TWO) {
+                    const float o1 = __shfl_xor_sync(0xffffffffu, x1, j);
+                    x0 = take_min ? fminf(x0, o0) : fmaxf(x0, o0);
+                    x1 = take_min ? fmaxf(x1, o1) : fminf(x1, o1);  // descending
+                } else {
+                    x0 = take_min ? fminf(x0, o0) : fmaxf(x0, o0);
+                }
+            }
+        }
+        float tau;
+        if constexpr (TWO)
+            tau = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(fminf(x0, x1))));  // L = 32
+        else
+            tau = __shfl_sync(0xffffffffu, x0, L - 1);
+        const bool v0 = lane < nc, v1 = TWO && lane + 32 < nc;
+        const uint32_t lt0 = __ballot_sync(0xffffffffu, v0 && cm0 < tau);
+        const uint32_t lt1 = TWO ? __ballot_sync(0xffffffffu, v1 && cm1 < tau) : 0u;
+        const uint32_t eq0 = __ballot_sync(0xffffffffu, v0 && cm0 == tau);
+        const uint32_t eq1 = TWO ? __ballot_sync(0xffffffffu, v1 && cm1 == tau) : 0u;
+        const int need = L - __popc(lt0) - __popc(lt1);
+        km0 = lt0 | __ballot_sync(0xffffffffu, ((eq0 >> lane) & 1u) && __popc(eq0 & below) < need);
+        if constexpr (TWO)
+            km1 = lt1 | __ballot_sync(0xffffffffu, ((eq1 >> lane) & 1u) && __popc(eq0) + __popc(eq1 & below) < need);
+    } else {
+        // few candidates (at most 16, one per lane): rank by counting
+        int rank0 = 0;
+#pragma unroll 8
+        for (int c2 = 0; c2 < nc; ++c2) {
+            const float o = __shfl_sync(0xffffffffu, cm0, c2);
+            rank0 += (o < cm0) || (o == cm0 && c2 < lane);
+        }
+        km0 = __ballot_sync(0xffffffffu, lane < nc && rank0 < L);
+    }
     if (km0 & (1u << lane)) selc[__popc(km0 & below)] = (uint8_t)lane;
     if (TWO && (km1 & (1u << lane))) selc[__popc(km0) + __popc(km1 & below)] = (uint8_t)(lane + 32);
     dup = ((km0 & (km0 >> 1) & 0x55555555u) | (km1 & (km1 >> 1) & 0x55555555u)) != 0u;
