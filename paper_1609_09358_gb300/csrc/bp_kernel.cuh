@@ -342,13 +342,13 @@ __device__ __forceinline__ WRow<E, R> wms_ones()
 
 template <int LOGN>
 struct BPConfig;  // thread plan and frames (or frame pairs) per CTA for each block length
-// MIN_CTAS: resident CTAs per SM the register allocation of the plain kernel must allow (launch
-// bounds; the weighted kernel would spill)
-template <> struct BPConfig<7>  { using Plan = BPPlan<7, 2>;  static constexpr int F = 4, MIN_CTAS = 1; };
-template <> struct BPConfig<8>  { using Plan = BPPlan<8, 3>;  static constexpr int F = 4, MIN_CTAS = 1; };
-template <> struct BPConfig<9>  { using Plan = BPPlan<9, 3>;  static constexpr int F = 1, MIN_CTAS = 1; };
-template <> struct BPConfig<10> { using Plan = BPPlan<10, 3>; static constexpr int F = 1, MIN_CTAS = 4; };
-template <> struct BPConfig<11> { using Plan = BPPlan<11, 3>; static constexpr int F = 1, MIN_CTAS = 2; };
+// MIN_CTAS / MIN_CTAS_W: resident CTAs per SM the register allocation of the plain / weighted
+// kernel must allow (launch bounds)
+template <> struct BPConfig<7>  { using Plan = BPPlan<7, 2>;  static constexpr int F = 4, MIN_CTAS = 4, MIN_CTAS_W = 4; };
+template <> struct BPConfig<8>  { using Plan = BPPlan<8, 3>;  static constexpr int F = 4, MIN_CTAS = 4, MIN_CTAS_W = 3; };
+template <> struct BPConfig<9>  { using Plan = BPPlan<9, 3>;  static constexpr int F = 1, MIN_CTAS = 8, MIN_CTAS_W = 5; };
+template <> struct BPConfig<10> { using Plan = BPPlan<10, 3>; static constexpr int F = 1, MIN_CTAS = 4, MIN_CTAS_W = 3; };
+template <> struct BPConfig<11> { using Plan = BPPlan<11, 3>; static constexpr int F = 1, MIN_CTAS = 2, MIN_CTAS_W = 1; };
 
 template <class P>
 __host__ __device__ constexpr int bp_slot_words()
@@ -360,7 +360,8 @@ __host__ __device__ constexpr int bp_slot_words()
 
 // One frame group of T threads decoding frames from `src` until it runs dry.  Group `slot` of
 // the CTA uses the shared-memory slice `slot_smem` (bp_slot_words<P>() words).
-template <class P, class MSG, bool WEIGHTED, bool SHARED_CTA, class Src>
+// SYNP (half2 only): both frames' CRC syndromes in one word -- for CRCs of at most 16 bits.
+template <class P, class MSG, bool WEIGHTED, bool SHARED_CTA, class Src, bool SYNP = false>
 __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, int slot, int t, uint32_t* slot_smem,
                                              Src& src)
 {
@@ -394,10 +395,15 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 
     MSG Lc[n + 2][R];
     MSG Rc[n + 2][R];
+    // SYNP: both frames' syndromes share one word (frame 0 in the low half, frame 1 in the high
+    // half), the columns are stored doubled
+    static_assert(!SYNP || FPT == 2, "packed syndromes are for half2 messages");
+    constexpr bool syn_packed = SYNP;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const int j = P::node(0, t, k);
-        csyn[k * T + t] = C.colsyn[j];
+        const uint32_t col = C.colsyn[j];
+        csyn[k * T + t] = syn_packed ? (col | (col << 16)) : col;
         Rc[1][k] = frozen_at(C.frozen_bits, j) ? Mv : MT::splat(0.0f);
     }
     {
@@ -604,29 +610,41 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                 // information nodes decided 1 (frozen nodes have column 0).  On an information
                 // node R[1] = +0, so u is never -0 and its sign bit is exactly (u < 0): the
                 // decision is an arithmetic shift and the update one and-xor.
+                if constexpr (syn_packed) {
+                    // one byte permute replicates the sign bits of both halves into a 16|16 mask
 #pragma unroll
-                for (int k = 0; k < R; ++k) {
-                    const MSG u = fadd(Lc[1][k], Rc[1][k]);
-                    const uint32_t col = csyn[k * T + t];
-                    uint32_t ub;
-                    memcpy(&ub, &u, 4);
-                    if constexpr (FPT == 2) {
-                        syn0 ^= col & (uint32_t)((int32_t)(ub << 16) >> 31);
-                        syn1 ^= col & (uint32_t)((int32_t)ub >> 31);
-                    } else {
-                        syn0 ^= col & (uint32_t)((int32_t)ub >> 31);
+                    for (int k = 0; k < R; ++k) {
+                        const MSG u = fadd(Lc[1][k], Rc[1][k]);
+                        uint32_t ub, m;
+                        memcpy(&ub, &u, 4);
+                        asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(m) : "r"(ub));
+                        syn0 ^= csyn[k * T + t] & m;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        const MSG u = fadd(Lc[1][k], Rc[1][k]);
+                        const uint32_t col = csyn[k * T + t];
+                        uint32_t ub;
+                        memcpy(&ub, &u, 4);
+                        if constexpr (FPT == 2) {
+                            syn0 ^= col & (uint32_t)((int32_t)(ub << 16) >> 31);
+                            syn1 ^= col & (uint32_t)((int32_t)ub >> 31);
+                        } else {
+                            syn0 ^= col & (uint32_t)((int32_t)ub >> 31);
+                        }
                     }
                 }
             }
         });
         // ------------------------------------------------------------------ CRC early stop
         syn0 = __reduce_xor_sync(0xffffffffu, syn0);
-        if constexpr (FPT == 2) syn1 = __reduce_xor_sync(0xffffffffu, syn1);
+        if constexpr (FPT == 2 && !syn_packed) syn1 = __reduce_xor_sync(0xffffffffu, syn1);
         if constexpr (NW > 1) {
             uint32_t* sp = synp + (it & 1) * 2 * NW;
             if ((t & 31) == 0) {
                 sp[t >> 5] = syn0;
-                if constexpr (FPT == 2) sp[NW + (t >> 5)] = syn1;
+                if constexpr (FPT == 2 && !syn_packed) sp[NW + (t >> 5)] = syn1;
             }
             group_sync<T, SHARED_CTA>(slot);
             syn0 = 0;
@@ -634,8 +652,12 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
                 syn0 ^= sp[w];
-                if constexpr (FPT == 2) syn1 ^= sp[NW + w];
+                if constexpr (FPT == 2 && !syn_packed) syn1 ^= sp[NW + w];
             }
+        }
+        if constexpr (syn_packed) {
+            syn1 = syn0 >> 16;
+            syn0 &= 0xFFFFu;
         }
         ++it;
         const uint32_t syn[2] = {syn0, syn1};
@@ -657,8 +679,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 
 // Per-length kernel: F frame groups per CTA; THREADS = F * T (passed explicitly: launch bounds
 // take no dependent member expression).
-template <int LOGN, class MSG, bool WEIGHTED, int THREADS>
-__global__ void __launch_bounds__(THREADS, WEIGHTED ? 1 : BPConfig<LOGN>::MIN_CTAS) bp_kernel(const BPArgs a)
+template <int LOGN, class MSG, bool WEIGHTED, int THREADS, bool SYNP = false>
+__global__ void __launch_bounds__(THREADS, WEIGHTED ? BPConfig<LOGN>::MIN_CTAS_W : BPConfig<LOGN>::MIN_CTAS) bp_kernel(const BPArgs a)
 {
     using P = typename BPConfig<LOGN>::Plan;
     constexpr int F = BPConfig<LOGN>::F;
@@ -669,7 +691,8 @@ __global__ void __launch_bounds__(THREADS, WEIGHTED ? 1 : BPConfig<LOGN>::MIN_CT
     const int t = threadIdx.x % P::T;
     constexpr int FPT = MsgTraits<MSG>::FPT;
     CounterSource src{a.next, a.B, (int)((blockIdx.x * F + slot) * FPT), FPT};
-    bp_run_group<P, MSG, WEIGHTED, false>(a, *a.code, slot, t, smem + slot * bp_slot_words<P>(), src);
+    bp_run_group<P, MSG, WEIGHTED, false, CounterSource, SYNP>(a, *a.code, slot, t, smem + slot * bp_slot_words<P>(),
+                                                               src);
 }
 
 }  // namespace polar

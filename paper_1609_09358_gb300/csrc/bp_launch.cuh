@@ -13,9 +13,10 @@ struct BPKernelInfo {
     int groups_per_cta;  // frame groups (frames, or frame pairs for half2) per CTA
 };
 
-// kernel of (log2 N, weighted) for the message type of this translation unit
+// kernel of (log2 N, weighted) for the message type of this translation unit; half2 plain
+// kernels come in a variant with both frames' CRC syndromes in one word (crc_len <= 16)
 BPKernelInfo bp_kernel_info_fp32(int logn, bool weighted);
-BPKernelInfo bp_kernel_info_fp16(int logn, bool weighted);
+BPKernelInfo bp_kernel_info_fp16(int logn, bool weighted, bool packed_syndrome);
 // natural-layout learned weights [iters][2][n][N] -> the prepared layout of the length's plan
 cudaError_t wms_prepare_fp32(int logn, const float* w, int iters, void* out, cudaStream_t st);
 cudaError_t wms_prepare_fp16(int logn, const float* w, int iters, void* out, cudaStream_t st);
@@ -42,7 +43,7 @@ cudaError_t wms_prepare_t(int logn, const float* w, int iters, void* out, cudaSt
 }
 
 template <class MSG>
-BPKernelInfo bp_kernel_info_t(int logn, bool weighted)
+BPKernelInfo bp_kernel_info_t(int logn, bool weighted, bool packed_syndrome = false)
 {
     auto pick = [&](auto LOGN_C) -> BPKernelInfo {
         constexpr int LOGN = decltype(LOGN_C)::value;
@@ -50,7 +51,14 @@ BPKernelInfo bp_kernel_info_t(int logn, bool weighted)
         using P = typename Cfg::Plan;
         constexpr int TH = Cfg::F * P::T;
         const size_t smem = (size_t)Cfg::F * bp_slot_words<P>() * 4;
-        const void* fn = weighted ? (const void*)bp_kernel<LOGN, MSG, true, TH> : (const void*)bp_kernel<LOGN, MSG, false, TH>;
+        const void* fn;
+        if (weighted)
+            fn = (const void*)bp_kernel<LOGN, MSG, true, TH>;
+        else if constexpr (std::is_same<MSG, __half2>::value)
+            fn = packed_syndrome ? (const void*)bp_kernel<LOGN, MSG, false, TH, true>
+                                 : (const void*)bp_kernel<LOGN, MSG, false, TH>;
+        else
+            fn = (const void*)bp_kernel<LOGN, MSG, false, TH>;
         return {fn, TH, smem, Cfg::F};
     };
     switch (logn) {

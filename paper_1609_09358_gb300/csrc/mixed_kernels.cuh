@@ -68,8 +68,10 @@ __device__ __forceinline__ void mix_run(const MixedArgs& m, int c, uint32_t* sme
     bp_run_group<P, MSG, false, (G > 1)>(m.base, *m.code[c], slot, t, smem + slot * bp_slot_words<P>(), src);
 }
 
+// FP32: two resident CTAs per SM (the register cap costs a few bytes of spill); half2 keeps one
+// (capping it spills hundreds of bytes)
 template <class MSG>
-__global__ void __launch_bounds__(kMixBlock, 1) bp_mixed_kernel(const MixedArgs m)
+__global__ void __launch_bounds__(kMixBlock, std::is_same<MSG, float>::value ? 2 : 1) bp_mixed_kernel(const MixedArgs m)
 {
     extern __shared__ uint32_t smem[];
     for (int k = 0; k < m.ncodes; ++k) {

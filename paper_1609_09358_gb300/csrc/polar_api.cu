@@ -311,7 +311,8 @@ static int launch_bp(const DevCode* dcode, const polar_code* code, const float* 
     const int n = log2i(code->N);
     if (B == 0) return POLAR_OK;
     if (n < 7 || n > 11) return fail(POLAR_ERR_ARG, "unsupported N = %d", code->N);
-    const BPKernelInfo k = precision == POLAR_FP16 ? bp_kernel_info_fp16(n, w != nullptr) : bp_kernel_info_fp32(n, w != nullptr);
+    const BPKernelInfo k = precision == POLAR_FP16 ? bp_kernel_info_fp16(n, w != nullptr, code->crc_len <= 16)
+                                                   : bp_kernel_info_fp32(n, w != nullptr);
     const int fpt = precision == POLAR_FP16 ? 2 : 1;
     const int groups = (B + fpt - 1) / fpt;
     const int F = k.groups_per_cta;
