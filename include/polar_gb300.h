@@ -49,6 +49,9 @@ extern "C" {
 /* ---------------------------------------------------------------- options */
 #define POLAR_FP32 0 /* BP messages in binary32 */
 #define POLAR_FP16 1 /* BP messages in binary16, two frames per half2 register */
+/* bp_decode only, OR-ed into precision: run exactly max_iters iterations (no CRC early stop);
+ * the status still reports whether the CRC of the final hard decision holds. */
+#define POLAR_FIXED_ITERS 0x100
 
 #define POLAR_OP_BP 0
 #define POLAR_OP_SCL 1
@@ -113,7 +116,7 @@ int polar_awgn_llr(const uint8_t* codeword, int32_t B, int32_t N, float sigma,
  * is CRC-checked and the frame stops when it passes.
  *   llr: device float [B][N].  max_iters >= 1.  llr_max > 0.
  *   precision: POLAR_FP32 (bit-exact with a binary32 reference) or POLAR_FP16 (binary16
- *     messages, llr_max <= 32768).
+ *     messages, llr_max <= 32768), optionally | POLAR_FIXED_ITERS.
  *   wms_scales: NULL, or the learned weights of a weighted min-sum BP as prepared by
  *     wms_prepare for this code, wms_iters and precision (device, 16-byte aligned): each g term
  *     is multiplied by its scale before the clip; iterations t >= wms_iters run unweighted.

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpolar_gb300.so")
 
 POLAR_OK = 0
 POLAR_FP32, POLAR_FP16 = 0, 1
+POLAR_FIXED_ITERS = 0x100  # bp_decode: OR into precision to run exactly max_iters iterations
 POLAR_OP_BP, POLAR_OP_SCL, POLAR_OP_HYBRID, POLAR_OP_HYBRID_HOST = 0, 1, 2, 3
 FRAME_BP_OK, FRAME_SCL_OK, FRAME_SCL_CRC_FAIL, FRAME_BP_FAIL = 1, 2, 3, 4
 CRC_POLYS = {0: 0x0, 8: 0x07, 16: 0x1021, 24: 0x864CFB}
@@ -256,7 +257,7 @@ def bp_decode(code: PolarCode, llr, max_iters: int, llr_max: float, precision: i
               iters, llr_u=None, llr_x=None, workspace=None, stream=None) -> None:
     """wms_scales: None, PreparedScales, or CUDA float32 weights [T][2][n][N] (prepared per call)."""
     B = llr.shape[0]
-    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision, stream)
+    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision & ~POLAR_FIXED_ITERS, stream)
     ws_b = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(load().bp_decode(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, wms_scales, w_iters,
                             _ptr(bits), _ptr(status), _ptr(iters), _ptr(llr_u), _ptr(llr_x), _ptr(workspace), ws_b,

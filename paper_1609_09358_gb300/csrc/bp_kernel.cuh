@@ -170,6 +170,7 @@ struct BPArgs {
     int* next;        // work counter (zero before the launch): groups refill from it; null = one frame group per CTA slot
     const long long* llr_off;  // element offset of each frame's LLR row (null: frame * N)
     int row_bytes;
+    int fixed_iters;           // run max_iters iterations regardless of the CRC
 };
 
 // Message traits: FP32 (one frame per thread) or half2 (two frames per thread).
@@ -667,7 +668,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             if (fr[h] < 0) continue;
             ++itc[h];
             const bool ok = syn[h] == 0u;
-            if (ok || itc[h] >= a.max_iters) {
+            if ((ok && !a.fixed_iters) || itc[h] >= a.max_iters) {
                 finalize(h, itc[h], ok);
                 refill(h);
             }

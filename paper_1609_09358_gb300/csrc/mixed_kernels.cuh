@@ -41,7 +41,7 @@ __host__ __device__ constexpr int mix_cta_words()
 }
 
 // Defined in mixed_launch.cu: the kernel of a precision, and the bucketing by code.
-const void* bp_mixed_fn(int precision);
+const void* bp_mixed_fn(int precision, bool packed_syndrome);
 cudaError_t mix_bucketing(const int* code_of, int B, int ncodes, int* counts, int* start, int* cursor, int* order,
                           cudaStream_t st);
 
@@ -59,19 +59,21 @@ inline size_t mix_smem_bytes(int variant)
 }
 
 #ifdef POLAR_MIXED_KERNELS
-template <class P, class MSG>
+template <class P, class MSG, bool SYNP>
 __device__ __forceinline__ void mix_run(const MixedArgs& m, int c, uint32_t* smem)
 {
     constexpr int G = kMixBlock / P::T;  // frame groups in the CTA
     const int slot = threadIdx.x / P::T, t = threadIdx.x % P::T;
     QueueSource src{m.order + m.start[c], m.start[c + 1] - m.start[c], m.qnext + c};
-    bp_run_group<P, MSG, false, (G > 1)>(m.base, *m.code[c], slot, t, smem + slot * bp_slot_words<P>(), src);
+    bp_run_group<P, MSG, false, (G > 1), QueueSource, SYNP>(m.base, *m.code[c], slot, t,
+                                                            smem + slot * bp_slot_words<P>(), src);
 }
 
-// FP32: two resident CTAs per SM (the register cap costs a few bytes of spill); half2 keeps one
-// (capping it spills hundreds of bytes)
-template <class MSG>
-__global__ void __launch_bounds__(kMixBlock, std::is_same<MSG, float>::value ? 2 : 1) bp_mixed_kernel(const MixedArgs m)
+// Two resident CTAs per SM (the register cap costs a few bytes of spill); the half2 kernel whose
+// codes have CRCs of at most 16 bits keeps both frames' syndromes in one word (SYNP)
+template <class MSG, bool SYNP>
+__global__ void __launch_bounds__(kMixBlock, (std::is_same<MSG, float>::value || SYNP) ? 2 : 1)
+    bp_mixed_kernel(const MixedArgs m)
 {
     extern __shared__ uint32_t smem[];
     for (int k = 0; k < m.ncodes; ++k) {
@@ -79,13 +81,13 @@ __global__ void __launch_bounds__(kMixBlock, std::is_same<MSG, float>::value ? 2
         // Every thread enters (control flow stays uniform over the CTA: a group's threads must all
         // reach its barriers); a group whose first fetch finds the queue empty returns at once.
         switch (m.variant[c]) {
-            case 0: mix_run<BPPlan<7, 2>, MSG>(m, c, smem); break;
-            case 1: mix_run<BPPlan<8, 3>, MSG>(m, c, smem); break;
-            case 2: mix_run<BPPlan<8, 2>, MSG>(m, c, smem); break;
-            case 3: mix_run<BPPlan<9, 3>, MSG>(m, c, smem); break;
-            case 4: mix_run<BPPlan<9, 2>, MSG>(m, c, smem); break;
-            case 5: mix_run<BPPlan<10, 3>, MSG>(m, c, smem); break;
-            default: mix_run<BPPlan<11, 3>, MSG>(m, c, smem); break;
+            case 0: mix_run<BPPlan<7, 2>, MSG, SYNP>(m, c, smem); break;
+            case 1: mix_run<BPPlan<8, 3>, MSG, SYNP>(m, c, smem); break;
+            case 2: mix_run<BPPlan<8, 2>, MSG, SYNP>(m, c, smem); break;
+            case 3: mix_run<BPPlan<9, 3>, MSG, SYNP>(m, c, smem); break;
+            case 4: mix_run<BPPlan<9, 2>, MSG, SYNP>(m, c, smem); break;
+            case 5: mix_run<BPPlan<10, 3>, MSG, SYNP>(m, c, smem); break;
+            default: mix_run<BPPlan<11, 3>, MSG, SYNP>(m, c, smem); break;
         }
         __syncthreads();
     }

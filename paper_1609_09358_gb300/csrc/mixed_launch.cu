@@ -5,9 +5,10 @@
 
 namespace polar {
 
-const void* bp_mixed_fn(int precision)
+const void* bp_mixed_fn(int precision, bool packed_syndrome)
 {
-    return precision == POLAR_FP16 ? (const void*)bp_mixed_kernel<__half2> : (const void*)bp_mixed_kernel<float>;
+    if (precision != POLAR_FP16) return (const void*)bp_mixed_kernel<float, false>;
+    return packed_syndrome ? (const void*)bp_mixed_kernel<__half2, true> : (const void*)bp_mixed_kernel<__half2, false>;
 }
 
 cudaError_t mix_bucketing(const int* code_of, int B, int ncodes, int* counts, int* start, int* cursor, int* order,

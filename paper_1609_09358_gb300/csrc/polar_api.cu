@@ -288,9 +288,10 @@ struct ProfScope {
 static int launch_bp(const DevCode* dcode, const polar_code* code, const float* llr, int B, int max_iters,
                      float llr_max, int precision, const void* w, int w_iters, uint8_t* bits, uint8_t* status,
                      uint16_t* iters, float* llr_u, float* llr_x, int* fail_count, int* fail_list,
-                     cudaStream_t stream, int* fail_total = nullptr, int* next = nullptr)
+                     cudaStream_t stream, int* fail_total = nullptr, int* next = nullptr, int fixed_iters = 0)
 {
     BPArgs a{};
+    a.fixed_iters = fixed_iters;
     a.fail_total = fail_total;
     a.next = next;
     a.llr = llr;
@@ -486,13 +487,15 @@ int bp_decode(const polar_code* code, const float* llr, int32_t B, int32_t max_i
 {
     (void)workspace;
     (void)ws;
+    const int fixed_iters = (precision & POLAR_FIXED_ITERS) != 0;
+    precision &= ~POLAR_FIXED_ITERS;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = check_bp_args(code, llr, B, max_iters, llr_max, precision, wms_scales, wms_iters, bits, status, iters);
     if (rc) return rc;
     const DevCode* d = nullptr;
     if ((rc = code_slot(code, st, &d))) return rc;
     return launch_bp(d, code, llr, B, max_iters, llr_max, precision, wms_scales, wms_iters, bits, status, iters,
-                     llr_u, llr_x, nullptr, nullptr, st);
+                     llr_u, llr_x, nullptr, nullptr, st, nullptr, nullptr, fixed_iters);
 }
 
 int scl_decode(const polar_code* code, const float* llr, int32_t B, int32_t L, uint8_t* bits, uint8_t* status,
@@ -785,12 +788,14 @@ int mix_bp(const polar_code* codes, int ncodes, const DevCode* const* dcodes, co
     m.start = start;
     m.qnext = qnext;
     size_t smem = 0;
+    bool packed = true;  // every code's CRC fits a 16-bit half of the syndrome word
     for (int c = 0; c < ncodes; ++c) {
         m.code[c] = dcodes[c];
         m.variant[c] = variants[c];
         smem = std::max(smem, mix_smem_bytes(variants[c]));
+        packed = packed && codes[c].crc_len <= 16;
     }
-    const void* fn = bp_mixed_fn(precision);
+    const void* fn = bp_mixed_fn(precision, packed);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "bp_mixed_kernel attribute");
     int per_sm = 0;

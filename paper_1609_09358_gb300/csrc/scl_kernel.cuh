@@ -60,7 +60,10 @@ struct SCLArgs {
 };
 
 __host__ __device__ inline int scl_cw(int k) { return k < 5 ? 1 : 1 << (k - 5); }  // words of a level-k C array
-__host__ __device__ inline int scl_cwsum(int k) { return k <= 5 ? k : 4 + (1 << (k - 5)); }  // sum of cw(q), q < k
+// Per-path stride of the level-k C arrays: one pad word beyond a single word makes the stride
+// odd, so the same word of different paths falls in different banks.
+__host__ __device__ inline int scl_cs(int k) { return scl_cw(k) > 1 ? scl_cw(k) + 1 : 1; }
+__host__ __device__ inline int scl_cssum(int k) { return k <= 5 ? k : (1 << (k - 5)) + k - 2; }  // sum of cs(q), q < k
 
 __host__ __device__ inline int log2_host(int v)
 {
@@ -81,7 +84,7 @@ struct SCLPlan {
 // then read into the path's registers.
 constexpr int kSclStage = 33;
 __host__ __device__ inline long long scl_smem_llr_words(int KS, int L) { return KS >= 6 ? (long long)L * ((2 << KS) - 64) : 0; }
-__host__ __device__ inline long long scl_smem_c_words(int KC, int L) { return KC >= 5 ? (long long)L * (scl_cwsum(KC + 1) - 5) : 0; }
+__host__ __device__ inline long long scl_smem_c_words(int KC, int L) { return KC >= 5 ? (long long)L * (scl_cssum(KC + 1) - 5) : 0; }
 __host__ __device__ inline SCLPlan scl_plan(int N, int L, bool all_smem)
 {
     const int n = log2_host(N);
@@ -98,7 +101,7 @@ __host__ __device__ inline SCLPlan scl_plan(int N, int L, bool all_smem)
     // [C levels 5..KC][LLR levels 6..KS][level-5 staging, L rows of 33 words][list scratch, 16 words]
     p.warp_words = (int)(scl_smem_llr_words(p.KS, L) + scl_smem_c_words(p.KC, L)) + L * kSclStage + 16;
     p.warp_words = (p.warp_words + 3) & ~3;
-    p.slot_words = (long long)L * (N - (2 << p.KS)) + (long long)L * (scl_cwsum(n + 1) - scl_cwsum(p.KC + 1));
+    p.slot_words = (long long)L * (N - (2 << p.KS)) + (long long)L * (scl_cssum(n + 1) - scl_cssum(p.KC + 1));
     return p;
 }
 inline bool scl_fits_smem(int N, int L) { return 4LL * scl_plan(N, L, true).warp_words <= 80 * 1024; }
@@ -162,7 +165,7 @@ struct SCLWarp {
     }
     __device__ __forceinline__ uint32_t* Cl(int k) const  // k >= 5
     {
-        return k <= KC ? sC + L * (scl_cwsum(k) - 5) : gC + L * (scl_cwsum(k) - scl_cwsum(KC + 1));
+        return k <= KC ? sC + L * (scl_cssum(k) - 5) : gC + L * (scl_cssum(k) - scl_cssum(KC + 1));
     }
 };
 
@@ -253,6 +256,38 @@ __device__ __forceinline__ void leaf_inherit(Leaf& f, int parent)
     if constexpr (leaf_live(R, 3)) leaf_copy<8>(f.l3, parent);
     if constexpr (leaf_live(R, 2)) leaf_copy<4>(f.l2, parent);
     if constexpr (leaf_live(R, 1)) leaf_copy<2>(f.l1, parent);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) f.c[k] = __shfl_sync(0xffffffffu, f.c[k], parent);
+}
+
+// The same inheritance with the bit index at run time: `live` = bit k-1 set when leaf level k is
+// live after bit r (leaf_live_mask); one copy of the code serves every bit of the block.
+// Closed form of the same table: level k is next touched at q, the first multiple of 2^(k-1) after
+// r; bit q reads it (by g) iff ctz(q) = k-1, rewrites it iff ctz(q) >= k.
+__host__ __device__ constexpr uint32_t leaf_live_mask(int r)
+{
+    uint32_t m = 0;
+    for (int k = 1; k <= 5; ++k) {
+        const int q = (r | ((1 << (k - 1)) - 1)) + 1;
+        if (q < 32 && ((q >> (k - 1)) & 1)) m |= 1u << (k - 1);
+    }
+    return m;
+}
+constexpr bool leaf_live_mask_matches()
+{
+    for (int r = 0; r < 32; ++r)
+        for (int k = 1; k <= 5; ++k)
+            if (((leaf_live_mask(r) >> (k - 1)) & 1u) != (leaf_live(r, k) ? 1u : 0u)) return false;
+    return true;
+}
+static_assert(leaf_live_mask_matches(), "closed form of the leaf liveness table");
+__device__ __forceinline__ void leaf_inherit_rt(Leaf& f, int parent, uint32_t live)
+{
+    if (live & 16u) leaf_copy<32>(f.l5, parent);
+    if (live & 8u) leaf_copy<16>(f.l4, parent);
+    if (live & 4u) leaf_copy<8>(f.l3, parent);
+    if (live & 2u) leaf_copy<4>(f.l2, parent);
+    if (live & 1u) leaf_copy<2>(f.l1, parent);
 #pragma unroll
     for (int k = 0; k < 5; ++k) f.c[k] = __shfl_sync(0xffffffffu, f.c[k], parent);
 }
@@ -423,7 +458,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             const uint32_t* cbk = S.Cl(k);
             const uint32_t my_d = stage ? (uint32_t)lane : fld(pA, k), my_s = from_ch ? 0u : fld(pA, k + 1),
                            my_c = fld(pC, k);
-            const int cwk = scl_cw(k), total = act << k;
+            const int cwk = scl_cs(k), total = act << k;
             // four elements per lane per round: all loads of a round are issued before any store,
             // so the L2 latency of the upper levels overlaps
             for (int e0 = 0; e0 < total; e0 += 128) {
@@ -489,6 +524,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                 bool dup = false;
                 parent = scl_list_step<TWO>(lam, pm, act, L, selc, bitv, dup, moved);
                 if (moved) {
+                    leaf_inherit_rt(lf, parent, leaf_live_mask(r));
                     pA[0] = __shfl_sync(0xffffffffu, pA[0], parent);
                     pA[1] = __shfl_sync(0xffffffffu, pA[1], parent);
                     pC[0] = __shfl_sync(0xffffffffu, pC[0], parent);
@@ -497,11 +533,8 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                 if (dup) shA = shC = 0xffffffffu;
             }
             switch (r) {
-#define SCL_LEAF_POST(R)                           \
-    case R:                                        \
-        if (moved) leaf_inherit<R>(lf, parent);    \
-        v5 = leaf_psum<R>(lf, bitv);               \
-        break;
+#define SCL_LEAF_POST(R) \
+    case R: v5 = leaf_psum<R>(lf, bitv); break;
                 SCL_FOR_32(SCL_LEAF_POST)
 #undef SCL_LEAF_POST
             }
@@ -515,7 +548,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                 shC &= ~(1u << kc);
             }
             uint32_t* dstl = S.Cl(kc);
-            const int cwk = scl_cw(kc);
+            const int cwk = scl_cs(kc);
             if (lane < act) dstl[fld(pC, kc) * cwk] = v5;
             __syncwarp();
             const uint32_t my_dst = fld(pC, kc);
@@ -533,7 +566,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                         uint32_t* dst = dstl + pd * cwk;
                         const uint32_t x = dst[w];
                         dst[W + w] = x;
-                        dst[w] = x ^ ckb[pk * scl_cw(k) + w];
+                        dst[w] = x ^ ckb[pk * scl_cs(k) + w];
                     }
                 }
                 __syncwarp();
@@ -548,7 +581,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
     const uint32_t my_x = fld(pC, n);
     uint32_t synd = 0xffffffffu;  // lane p: syndrome of path p
     for (int p = 0; p < act; ++p) {
-        uint32_t* xw = xl + __shfl_sync(0xffffffffu, my_x, p) * words;
+        uint32_t* xw = xl + __shfl_sync(0xffffffffu, my_x, p) * scl_cs(n);
         uint32_t w[2] = {0u, 0u};
 #pragma unroll
         for (int h = 0; h < 2; ++h)
@@ -599,7 +632,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             who = ow;
         }
     }
-    const uint32_t* uw = xl + __shfl_sync(0xffffffffu, my_x, who & 31) * words;
+    const uint32_t* uw = xl + __shfl_sync(0xffffffffu, my_x, who & 31) * scl_cs(n);
     uint8_t* out = a.bits + (size_t)frame * a.row_bytes;
     for (int by = lane; by < a.row_bytes; by += 32) {
         uint32_t v = 0u;
