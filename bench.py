@@ -322,6 +322,8 @@ def main():
             "bp_ms_per_step": bp_ms / a.steps, "scl_ms_per_step": scl_ms / a.steps,
             "gpu_launches": bp_n + scl_n, "roofline": roofline, "clocks": clocks}
 
+    if prec == api.POLAR_FP32 and not a.no_learned:
+        line["plain_fp16"] = plain_fp16(a, code, llr, payload, stream, dist)
     if not a.no_learned and os.path.exists(a.weights):
         line["learned_fp16"] = learned(a, llr, payload, stream, dist)
         line["learned_fp16_imax%d" % IMAX] = learned(a, llr, payload, stream, dist, IMAX)
@@ -337,6 +339,45 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def plain_fp16(a, code, llr, payload, stream, dist):
+    """The plain half2 form on the same frames: binary16 BP messages (clip 32), i_max = 200, then
+    CA-SCL L = 8 in FP32 on the CRC failures."""
+    import torch
+
+    from paper_1609_09358_gb300 import api
+    B = llr.shape[0]
+    dec = api.Decoder(code, B, LIST, device=llr.device)
+
+    def step():
+        dec.hybrid(llr, IMAX, 32.0, api.POLAR_FP16)
+
+    for _ in range(max(a.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    steps = max(1, min(a.steps, 50))
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    api.polar_profile_enable(True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    api.polar_profile_enable(False)
+    bp_ms, _, scl_ms, _ = api.polar_profile_read()
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=llr.device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    world = dist.get_world_size() if dist else 1
+    ferr = (dec.bits != payload).any(dim=1)
+    return {"value": world * code.P * B * steps / (float(t.item()) * 1e-3) / 1e9, "unit": "Gbit/s", "steps": steps,
+            "ms_per_step": float(t.item()) / steps, "fer": float(ferr.float().mean().item()),
+            "fallback_rate": float((dec.status != api.FRAME_BP_OK).float().mean().item()),
+            "avg_bp_iters": float(dec.iters.float().mean().item()), "i_max": IMAX,
+            "bp_ms_per_step": bp_ms / steps, "scl_ms_per_step": scl_ms / steps, "dtype": "f16"}
 
 
 def learned(a, llr, payload, stream, dist, imax=None):
