@@ -215,15 +215,18 @@ int polar_mixed_autotune(const polar_code* codes, int32_t ncodes, const int32_t*
 
 /* hybrid_decode on frames that live in host memory (not a step of the paper; its Sec. III
  * rejects moving SCL to the CPU because of transfer latency, which is what this hides).  The
- * batch is cut into chunks of up to POLAR_HOST_CHUNK frames; each chunk's LLRs are copied to the
- * device, decoded as in hybrid_decode and its results copied back, chunks alternating between
- * `stream` and a second library-owned stream so that copies of one chunk overlap the decoding of
- * the other.  The call is ordered after earlier work on `stream` and later work on `stream` is
- * ordered after it; it returns before completion when the host buffers are page-locked.
+ * LLRs are copied to the device in chunks of up to POLAR_HOST_CHUNK frames on a library-owned
+ * copy stream; each chunk's BP launch starts as soon as its own copy has landed (chunks
+ * alternating between `stream` and a second library-owned stream, so one chunk's last frames
+ * overlap the next), all chunks append to one fail list, one CA-SCL launch decodes every frame BP
+ * failed, and one copy per output brings the results back.  The call is ordered after earlier
+ * work on `stream` and later work on `stream` is ordered after it; it returns before completion
+ * when the host buffers are page-locked.  The workspace holds the whole batch (about 4N bytes per
+ * frame plus the hybrid workspace).
  *   llr_host: host float [B][N]; bits_host [B][ceil(P/8)], status_host [B], iters_host [B]:
  *   host.  wms_scales: device or NULL.  workspace: device, >= polar_workspace_bytes(code, B, L,
  *   POLAR_OP_HYBRID_HOST). */
-#define POLAR_HOST_CHUNK 32768
+#define POLAR_HOST_CHUNK 16384
 int hybrid_decode_host(const polar_code* code, const float* llr_host, int32_t B, int32_t max_iters,
                        float llr_max, int32_t precision, const void* wms_scales, int32_t wms_iters,
                        int32_t L, uint8_t* bits_host, uint8_t* status_host, uint16_t* iters_host,

@@ -171,6 +171,7 @@ struct BPArgs {
     const long long* llr_off;  // element offset of each frame's LLR row (null: frame * N)
     int row_bytes;
     int fixed_iters;           // run max_iters iterations regardless of the CRC
+    int frame0;                // index of the launch's first frame (frames frame0 .. frame0 + B - 1)
 };
 
 // Message traits: FP32 (one frame per thread) or half2 (two frames per thread).
@@ -238,6 +239,7 @@ struct CounterSource {
     int B;
     int first;  // first static frame of the group
     int FPT;
+    int frame0;  // offset of the launch's frames
     int nfetch = 0;
     template <int T, bool SHARED_CTA>
     __device__ int fetch(int slot, int t, int* cell)
@@ -252,7 +254,7 @@ struct CounterSource {
             f = nfetch < FPT ? first + nfetch : B;
         }
         ++nfetch;
-        return f < B ? f : -1;
+        return f < B ? frame0 + f : -1;
     }
 };
 
@@ -691,7 +693,7 @@ __global__ void __launch_bounds__(THREADS, WEIGHTED ? BPConfig<LOGN>::MIN_CTAS_W
     const int slot = threadIdx.x / P::T;
     const int t = threadIdx.x % P::T;
     constexpr int FPT = MsgTraits<MSG>::FPT;
-    CounterSource src{a.next, a.B, (int)((blockIdx.x * F + slot) * FPT), FPT};
+    CounterSource src{a.next, a.B, (int)((blockIdx.x * F + slot) * FPT), FPT, a.frame0};
     bp_run_group<P, MSG, WEIGHTED, false, CounterSource, SYNP>(a, *a.code, slot, t, smem + slot * bp_slot_words<P>(),
                                                                src);
 }

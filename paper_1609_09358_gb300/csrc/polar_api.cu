@@ -182,26 +182,29 @@ struct ChunkHdr {
 };
 static size_t hybrid_chunk_header_bytes(int) { return 256; }
 
-// One chunk's device buffers of hybrid_decode_host: LLRs, bits, status, iterations, hybrid
-// workspace; two such sets alternate.
+// Device buffers of hybrid_decode_host: the whole batch's LLRs, bits, status and iterations, the
+// BP work counters of the chunks, and the hybrid workspace of the batch.
 struct HostSet {
-    size_t llr, bits, status, iters, ws, ws_bytes, total;
+    size_t llr, bits, status, iters, counters, ws, ws_bytes, total;
 };
-static HostSet host_set_layout(const polar_code* code, int chunk, int L)
+static int host_chunks(int B) { return std::max(1, (B + POLAR_HOST_CHUNK - 1) / POLAR_HOST_CHUNK); }
+static HostSet host_set_layout(const polar_code* code, int B, int L)
 {
     HostSet h{};
     const size_t row = (size_t)(code->K - code->crc_len + 7) / 8;
     size_t o = 0;
     h.llr = o;
-    o = align_up(o + (size_t)chunk * code->N * sizeof(float), 256);
+    o = align_up(o + (size_t)B * code->N * sizeof(float), 256);
     h.bits = o;
-    o = align_up(o + (size_t)chunk * row, 256);
+    o = align_up(o + (size_t)B * row, 256);
     h.status = o;
-    o = align_up(o + (size_t)chunk, 256);
+    o = align_up(o + (size_t)B, 256);
     h.iters = o;
-    o = align_up(o + (size_t)chunk * sizeof(uint16_t), 256);
+    o = align_up(o + (size_t)B * sizeof(uint16_t), 256);
+    h.counters = o;
+    o = align_up(o + sizeof(int) * (size_t)host_chunks(B), 256);
     h.ws = o;
-    h.ws_bytes = ws_bytes(code, chunk, L, POLAR_OP_HYBRID);
+    h.ws_bytes = ws_bytes(code, B, L, POLAR_OP_HYBRID);
     o = align_up(o + h.ws_bytes, 256);
     h.total = o;
     return h;
@@ -210,10 +213,7 @@ static HostSet host_set_layout(const polar_code* code, int chunk, int L)
 static size_t ws_bytes(const polar_code* code, int B, int L, int op)
 {
     if (op == POLAR_OP_BP) return 0;
-    if (op == POLAR_OP_HYBRID_HOST) {
-        const int chunk = std::max(1, std::min(B, POLAR_HOST_CHUNK));
-        return 2 * host_set_layout(code, chunk, L).total;
-    }
+    if (op == POLAR_OP_HYBRID_HOST) return host_set_layout(code, std::max(B, 1), L).total;
     size_t b = kHeaderBytes;
     if (op == POLAR_OP_HYBRID) {
         b += hybrid_chunk_header_bytes(B);
@@ -223,17 +223,19 @@ static size_t ws_bytes(const polar_code* code, int B, int L, int op)
     return b;
 }
 
-// library-owned second stream per device for hybrid_decode_host
+// library-owned streams per device for hybrid_decode_host: [0] a second compute stream, [1] the
+// copy stream
 static std::mutex g_aux_mutex;
 static std::vector<cudaStream_t> g_aux;
-static int aux_stream(cudaStream_t* out)
+static int aux_stream(int which, cudaStream_t* out)
 {
     int dev = 0;
     POLAR_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(g_aux_mutex);
-    if ((int)g_aux.size() <= dev) g_aux.resize(dev + 1, nullptr);
-    if (!g_aux[dev]) POLAR_CUDA(cudaStreamCreateWithFlags(&g_aux[dev], cudaStreamNonBlocking));
-    *out = g_aux[dev];
+    if ((int)g_aux.size() <= 2 * dev + which) g_aux.resize(2 * dev + 2, nullptr);
+    cudaStream_t& sref = g_aux[2 * dev + which];
+    if (!sref) POLAR_CUDA(cudaStreamCreateWithFlags(&sref, cudaStreamNonBlocking));
+    *out = sref;
     return POLAR_OK;
 }
 
@@ -288,9 +290,11 @@ struct ProfScope {
 static int launch_bp(const DevCode* dcode, const polar_code* code, const float* llr, int B, int max_iters,
                      float llr_max, int precision, const void* w, int w_iters, uint8_t* bits, uint8_t* status,
                      uint16_t* iters, float* llr_u, float* llr_x, int* fail_count, int* fail_list,
-                     cudaStream_t stream, int* fail_total = nullptr, int* next = nullptr, int fixed_iters = 0)
+                     cudaStream_t stream, int* fail_total = nullptr, int* next = nullptr, int fixed_iters = 0,
+                     int frame0 = 0)
 {
     BPArgs a{};
+    a.frame0 = frame0;
     a.fixed_iters = fixed_iters;
     a.fail_total = fail_total;
     a.next = next;
@@ -559,40 +563,63 @@ int hybrid_decode_host(const polar_code* code, const float* llr_host, int32_t B,
     if (B == 0) return POLAR_OK;
     const size_t need = ws_bytes(code, B, L, POLAR_OP_HYBRID_HOST);
     if (!workspace || ws < need) return fail(POLAR_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws, need);
-    cudaStream_t st1 = nullptr;
-    if ((rc = aux_stream(&st1))) return rc;
-    const int chunk = std::min(B, POLAR_HOST_CHUNK);
-    const HostSet hs = host_set_layout(code, chunk, L);
+    cudaStream_t st1 = nullptr, stc = nullptr;
+    if ((rc = aux_stream(0, &st1)) || (rc = aux_stream(1, &stc))) return rc;
+    const HostSet hs = host_set_layout(code, B, L);
     const size_t N = (size_t)code->N, row = (size_t)(code->K - code->crc_len + 7) / 8;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    POLAR_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
-    POLAR_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
-    POLAR_CUDA(cudaEventRecord(ev_in, st0));
-    POLAR_CUDA(cudaStreamWaitEvent(st1, ev_in, 0));
+    char* base = static_cast<char*>(workspace);
+    float* llr_d = reinterpret_cast<float*>(base + hs.llr);
+    uint8_t* bits_d = reinterpret_cast<uint8_t*>(base + hs.bits);
+    uint8_t* status_d = reinterpret_cast<uint8_t*>(base + hs.status);
+    uint16_t* iters_d = reinterpret_cast<uint16_t*>(base + hs.iters);
+    int* counters = reinterpret_cast<int*>(base + hs.counters);
+    char* wsb = base + hs.ws;
+    int* total = reinterpret_cast<int*>(wsb);
+    ChunkHdr* hdr = reinterpret_cast<ChunkHdr*>(wsb + kHeaderBytes);
+    int* list = reinterpret_cast<int*>(wsb + kHeaderBytes + hybrid_chunk_header_bytes(B));
+    void* scratch = reinterpret_cast<char*>(list) + align_up(sizeof(int) * (size_t)B, 256);
+    const int nchunks = host_chunks(B);
+    POLAR_CUDA(cudaMemsetAsync(wsb, 0, kHeaderBytes + sizeof(ChunkHdr), st0));
+    POLAR_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * (size_t)nchunks, st0));
+    std::vector<cudaEvent_t> evs;
+    auto event = [&](cudaEvent_t* e) -> int {
+        POLAR_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        evs.push_back(*e);
+        return POLAR_OK;
+    };
+    // The copy stream runs ahead, chunk by chunk; each chunk's BP launch waits for its own copy only,
+    // and the chunks alternate between two compute streams (one chunk's last frames overlap the next
+    // chunk).  One CA-SCL launch then takes every frame BP failed, and one copy brings the results
+    // back.
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if ((rc = event(&ev0))) return rc;
+    POLAR_CUDA(cudaEventRecord(ev0, st0));
+    POLAR_CUDA(cudaStreamWaitEvent(stc, ev0, 0));
+    POLAR_CUDA(cudaStreamWaitEvent(st1, ev0, 0));
     const cudaStream_t sts[2] = {st0, st1};
-    for (int c = 0, b0 = 0; b0 < B; ++c, b0 += chunk) {
-        const int nb = std::min(chunk, B - b0);
+    for (int c = 0; c < nchunks && rc == POLAR_OK; ++c) {
+        const int b0 = c * POLAR_HOST_CHUNK, nb = std::min(POLAR_HOST_CHUNK, B - b0);
         const cudaStream_t st = sts[c & 1];
-        char* base = static_cast<char*>(workspace) + (size_t)(c & 1) * hs.total;
-        float* llr_d = reinterpret_cast<float*>(base + hs.llr);
-        uint8_t* bits_d = reinterpret_cast<uint8_t*>(base + hs.bits);
-        uint8_t* status_d = reinterpret_cast<uint8_t*>(base + hs.status);
-        uint16_t* iters_d = reinterpret_cast<uint16_t*>(base + hs.iters);
-        POLAR_CUDA(cudaMemcpyAsync(llr_d, llr_host + (size_t)b0 * N, (size_t)nb * N * sizeof(float),
-                                   cudaMemcpyHostToDevice, st));
-        rc = hybrid_decode(code, llr_d, nb, max_iters, llr_max, precision, wms_scales, wms_iters, L, bits_d, status_d,
-                           iters_d, base + hs.ws, hs.ws_bytes, st);
-        if (rc) break;
-        if (row) POLAR_CUDA(cudaMemcpyAsync(bits_host + (size_t)b0 * row, bits_d, (size_t)nb * row,
-                                            cudaMemcpyDeviceToHost, st));
-        POLAR_CUDA(cudaMemcpyAsync(status_host + b0, status_d, (size_t)nb, cudaMemcpyDeviceToHost, st));
-        POLAR_CUDA(cudaMemcpyAsync(iters_host + b0, iters_d, (size_t)nb * sizeof(uint16_t), cudaMemcpyDeviceToHost,
-                                   st));
+        cudaEvent_t evc = nullptr;
+        if ((rc = event(&evc))) break;
+        POLAR_CUDA(cudaMemcpyAsync(llr_d + (size_t)b0 * N, llr_host + (size_t)b0 * N, (size_t)nb * N * sizeof(float),
+                                   cudaMemcpyHostToDevice, stc));
+        POLAR_CUDA(cudaEventRecord(evc, stc));
+        POLAR_CUDA(cudaStreamWaitEvent(st, evc, 0));
+        rc = launch_bp(d, code, llr_d, nb, max_iters, llr_max, precision, wms_scales, wms_iters, bits_d, status_d,
+                       iters_d, nullptr, nullptr, &hdr->fail_count, list, st, total, counters + c, 0, b0);
     }
-    POLAR_CUDA(cudaEventRecord(ev_out, st1));
-    POLAR_CUDA(cudaStreamWaitEvent(st0, ev_out, 0));
-    cudaEventDestroy(ev_in);
-    cudaEventDestroy(ev_out);
+    if (rc == POLAR_OK && (rc = event(&ev1)) == POLAR_OK) {
+        POLAR_CUDA(cudaEventRecord(ev1, st1));
+        POLAR_CUDA(cudaStreamWaitEvent(st0, ev1, 0));
+        rc = launch_scl(d, code, llr_d, B, L, bits_d, status_d, list, &hdr->fail_count, &hdr->scl_next, scratch, st0);
+    }
+    if (rc == POLAR_OK) {
+        if (row) POLAR_CUDA(cudaMemcpyAsync(bits_host, bits_d, (size_t)B * row, cudaMemcpyDeviceToHost, st0));
+        POLAR_CUDA(cudaMemcpyAsync(status_host, status_d, (size_t)B, cudaMemcpyDeviceToHost, st0));
+        POLAR_CUDA(cudaMemcpyAsync(iters_host, iters_d, (size_t)B * sizeof(uint16_t), cudaMemcpyDeviceToHost, st0));
+    }
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
     return rc;
 }
 
