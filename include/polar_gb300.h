@@ -215,8 +215,8 @@ int polar_mixed_autotune(const polar_code* codes, int32_t ncodes, const int32_t*
 
 /* hybrid_decode on frames that live in host memory (not a step of the paper; its Sec. III
  * rejects moving SCL to the CPU because of transfer latency, which is what this hides).  The
- * LLRs are copied to the device in chunks of up to POLAR_HOST_CHUNK frames on a library-owned
- * copy stream; each chunk's BP launch starts as soon as its own copy has landed (chunks
+ * LLRs are copied to the device in chunks (4096 and 8192 frames, then POLAR_HOST_CHUNK) on a
+ * library-owned copy stream; each chunk's BP launch starts as soon as its own copy has landed (chunks
  * alternating between `stream` and a second library-owned stream, so one chunk's last frames
  * overlap the next), all chunks append to one fail list, one CA-SCL launch decodes every frame BP
  * failed, and one copy per output brings the results back.  The call is ordered after earlier

@@ -187,7 +187,15 @@ static size_t hybrid_chunk_header_bytes(int) { return 256; }
 struct HostSet {
     size_t llr, bits, status, iters, counters, ws, ws_bytes, total;
 };
-static int host_chunks(int B) { return std::max(1, (B + POLAR_HOST_CHUNK - 1) / POLAR_HOST_CHUNK); }
+// Chunk c of hybrid_decode_host: sizes 4096, 8192, then POLAR_HOST_CHUNK frames (small first
+// chunks so that BP starts early), the last one ragged.
+static int host_chunk_size(int c) { return std::min(POLAR_HOST_CHUNK, 4096 << std::min(c, 8)); }
+static int host_chunks(int B)
+{
+    int c = 0;
+    for (int b0 = 0; b0 < B; ++c) b0 += host_chunk_size(c);
+    return std::max(1, c);
+}
 static HostSet host_set_layout(const polar_code* code, int B, int L)
 {
     HostSet h{};
@@ -597,8 +605,8 @@ int hybrid_decode_host(const polar_code* code, const float* llr_host, int32_t B,
     POLAR_CUDA(cudaStreamWaitEvent(stc, ev0, 0));
     POLAR_CUDA(cudaStreamWaitEvent(st1, ev0, 0));
     const cudaStream_t sts[2] = {st0, st1};
-    for (int c = 0; c < nchunks && rc == POLAR_OK; ++c) {
-        const int b0 = c * POLAR_HOST_CHUNK, nb = std::min(POLAR_HOST_CHUNK, B - b0);
+    for (int c = 0, b0 = 0; c < nchunks && rc == POLAR_OK; b0 += host_chunk_size(c), ++c) {
+        const int nb = std::min(host_chunk_size(c), B - b0);
         const cudaStream_t st = sts[c & 1];
         cudaEvent_t evc = nullptr;
         if ((rc = event(&evc))) break;

@@ -52,7 +52,8 @@ struct SCLArgs {
     int row_bytes;
     int KS, KC;        // last LLR / partial-sum level kept in shared memory (single code)
     int warp_words;    // shared-memory words per warp
-    long long slot_words;  // global words per warp
+    int list_words;    // shared-memory words per list (two lists per warp when L <= 8)
+    long long slot_words;  // global words per list
     // several codes in one batch: code_of[frame] selects codes[], llr_off[frame] the LLR row
     const int* code_of;
     const long long* llr_off;
@@ -76,7 +77,7 @@ __host__ __device__ inline int log2_host(int v)
 // partial-sum levels 5..KC in shared memory, the rest in the warp's global slot.
 struct SCLPlan {
     int KS, KC;
-    int warp_words;
+    int warp_words, list_words;
     long long slot_words;
 };
 // Level 5 of every path is computed element-parallel into a staging row per path (33 words: the
@@ -85,7 +86,9 @@ struct SCLPlan {
 constexpr int kSclStage = 33;
 __host__ __device__ inline long long scl_smem_llr_words(int KS, int L) { return KS >= 6 ? (long long)L * ((2 << KS) - 64) : 0; }
 __host__ __device__ inline long long scl_smem_c_words(int KC, int L) { return KC >= 5 ? (long long)L * (scl_cssum(KC + 1) - 5) : 0; }
-__host__ __device__ inline SCLPlan scl_plan(int N, int L, bool all_smem)
+// `lists` = frames per warp (1, or 2 with half-warp lists): the shared-memory budget of a frame
+// is divided by it.
+__host__ __device__ inline SCLPlan scl_plan(int N, int L, bool all_smem, int lists = 1)
 {
     const int n = log2_host(N);
     SCLPlan p{};
@@ -94,13 +97,15 @@ __host__ __device__ inline SCLPlan scl_plan(int N, int L, bool all_smem)
         p.KC = n;
     } else {
         p.KS = 5;
-        while (p.KS + 1 <= n - 1 && 4 * scl_smem_llr_words(p.KS + 1, L) <= 6144) ++p.KS;
+        while (p.KS + 1 <= n - 1 && 4 * scl_smem_llr_words(p.KS + 1, L) * lists <= 6144) ++p.KS;
         p.KC = 4;
-        while (p.KC + 1 <= n && 4 * scl_smem_c_words(p.KC + 1, L) <= 2048) ++p.KC;
+        while (p.KC + 1 <= n && 4 * scl_smem_c_words(p.KC + 1, L) * lists <= 2048) ++p.KC;
     }
-    // [C levels 5..KC][LLR levels 6..KS][level-5 staging, L rows of 33 words][list scratch, 16 words]
-    p.warp_words = (int)(scl_smem_llr_words(p.KS, L) + scl_smem_c_words(p.KC, L)) + L * kSclStage + 16;
-    p.warp_words = (p.warp_words + 3) & ~3;
+    // per list: [C levels 5..KC][LLR levels 6..KS][level-5 staging, L rows of 33 words]; per warp:
+    // the lists, then 16 words of list-step scratch
+    p.list_words = (int)(scl_smem_llr_words(p.KS, L) + scl_smem_c_words(p.KC, L)) + L * kSclStage;
+    p.list_words = (p.list_words + 3) & ~3;
+    p.warp_words = lists * p.list_words + 16;
     p.slot_words = (long long)L * (N - (2 << p.KS)) + (long long)L * (scl_cssum(n + 1) - scl_cssum(p.KC + 1));
     return p;
 }
@@ -114,11 +119,15 @@ inline int scl_sm_count()
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return sms > 0 ? sms : 1;
 }
-// global workspace of the SCL list arrays (one slot per resident warp)
+// List width of a CA-SCL launch: two frames per warp (half-warp lists) for L <= 8 in the global
+// layout with a single code.
+inline bool scl_two_lists(int L, bool all_smem, bool one_code) { return L <= 8 && !all_smem && one_code; }
+// global workspace of the SCL list arrays (one slot per resident list: up to kSclWarpsPerSM lists
+// per SM)
 inline size_t scl_scratch_bytes(int N, int L)
 {
-    const SCLPlan p = scl_plan(N, L, false);
-    return (size_t)scl_sm_count() * kSclWarpsPerSM * (size_t)p.slot_words * 4;
+    const long long w = std::max(scl_plan(N, L, false).slot_words, scl_plan(N, L, false, 2).slot_words);
+    return (size_t)scl_sm_count() * kSclWarpsPerSM * (size_t)w * 4;
 }
 
 __device__ __forceinline__ uint32_t fld(const uint32_t (&w)[2], int k) { return ((k < 6 ? w[0] : w[1]) >> (5 * (k % 6))) & 31u; }
@@ -131,19 +140,88 @@ __device__ __forceinline__ void set_fld(uint32_t (&w)[2], int k, uint32_t v)
         w[1] = (w[1] & ~(31u << s)) | (v << s);
 }
 
+// Lanes of one list: the whole warp (W = 32, one frame per warp) or one half of it (W = 16, two
+// frames per warp, lists of at most 8 paths).  Path p of the list sits in lane base + p.  Every
+// collective below is executed by all 32 lanes; with W = 16 the two halves compute their own
+// results (shuffle offsets below 16 stay within a half).
+template <int W>
+struct Lanes {
+    int lane, pl, base;
+    __device__ __forceinline__ Lanes() : lane(threadIdx.x & 31), pl(lane & (W - 1)), base(lane & ~(W - 1)) {}
+    __device__ __forceinline__ uint32_t ballot(bool p) const
+    {
+        const uint32_t b = __ballot_sync(0xffffffffu, p);
+        return W == 32 ? b : (b >> base) & 0xffffu;
+    }
+    template <class V>
+    __device__ __forceinline__ V shfl(V v, int p) const { return __shfl_sync(0xffffffffu, v, base + p); }
+    __device__ __forceinline__ uint32_t red_or(uint32_t v) const
+    {
+        if constexpr (W == 32) {
+            return __reduce_or_sync(0xffffffffu, v);
+        } else {
+#pragma unroll
+            for (int o = W / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+            return v;
+        }
+    }
+    __device__ __forceinline__ uint32_t red_xor(uint32_t v) const
+    {
+        if constexpr (W == 32) {
+            return __reduce_xor_sync(0xffffffffu, v);
+        } else {
+#pragma unroll
+            for (int o = W / 2; o > 0; o >>= 1) v ^= __shfl_xor_sync(0xffffffffu, v, o);
+            return v;
+        }
+    }
+    __device__ __forceinline__ uint32_t red_max(uint32_t v) const
+    {
+        if constexpr (W == 32) {
+            return __reduce_max_sync(0xffffffffu, v);
+        } else {
+#pragma unroll
+            for (int o = W / 2; o > 0; o >>= 1) v = max(v, (uint32_t)__shfl_xor_sync(0xffffffffu, v, o));
+            return v;
+        }
+    }
+    __device__ __forceinline__ uint32_t red_min(uint32_t v) const
+    {
+        if constexpr (W == 32) {
+            return __reduce_min_sync(0xffffffffu, v);
+        } else {
+#pragma unroll
+            for (int o = W / 2; o > 0; o >>= 1) v = min(v, (uint32_t)__shfl_xor_sync(0xffffffffu, v, o));
+            return v;
+        }
+    }
+    __device__ __forceinline__ uint32_t match_any(uint32_t v) const
+    {
+        const uint32_t m = __match_any_sync(0xffffffffu, W == 32 ? v : v | ((uint32_t)base << 8));
+        return W == 32 ? m : (m >> base) & 0xffffu;
+    }
+    // the larger of the two lists' values (W = 16), for loop bounds every lane must share
+    __device__ __forceinline__ int both_max(int v) const
+    {
+        return W == 32 ? v : max(v, __shfl_xor_sync(0xffffffffu, v, 16));
+    }
+};
+
 // A path about to rewrite level k that it shares takes a free array of that level (lane = path;
-// `act` active paths; the lowest lane of each group of sharers keeps its array).
+// `act` active paths; the lowest lane of each group of sharers keeps its array).  A list without
+// sharing is left unchanged, so the call is safe for a list that does not need it.
+template <int W>
 __device__ __forceinline__ void scl_own(uint32_t (&w)[2], int k, int act, int L)
 {
-    const int lane = threadIdx.x & 31;
-    const bool on = lane < act;
-    const uint32_t mine = on ? fld(w, k) : 64u + lane;
-    const uint32_t same = __match_any_sync(0xffffffffu, mine);
-    const uint32_t below = (1u << lane) - 1u;
+    const Lanes<W> sg;
+    const bool on = sg.pl < act;
+    const uint32_t mine = on ? fld(w, k) : 64u + sg.pl;
+    const uint32_t same = sg.match_any(mine);
+    const uint32_t below = (1u << sg.pl) - 1u;
     const bool need = on && (same & below) != 0u;
-    const uint32_t used = __reduce_or_sync(0xffffffffu, on ? (1u << mine) : 0u);
+    const uint32_t used = sg.red_or(on ? (1u << mine) : 0u);
     uint32_t freem = ~used & (L >= 32 ? 0xffffffffu : ((1u << L) - 1u));
-    const int r = __popc(__ballot_sync(0xffffffffu, need) & below);
+    const int r = __popc(sg.ballot(need) & below);
     if (need) {
         for (int q = 0; q < r; ++q) freem &= freem - 1u;  // drop the r lowest free arrays
         set_fld(w, k, (uint32_t)(__ffs(freem) - 1));
@@ -424,15 +502,70 @@ __device__ __forceinline__ int scl_list_step(float lam, float& pm, int& act, int
     return cq >> 1;
 }
 
-template <bool TWO>  // TWO: L = 32, two candidates per lane
+// List step of a half-warp list (W = 16, L <= 8, at most 16 candidates, one per lane): the same
+// survivors as scl_list_step, computed with loop bounds shared by both halves -- the fast path is
+// taken only when both lists qualify, and the ranks count over all 2L candidate slots with the
+// unused ones at +inf.  Returns the survivor's parent path (within the list).
+__device__ __forceinline__ int scl_list_step_half(float lam, float& pm, int& act, int L, uint8_t* selc,
+                                                  uint32_t& bitv, bool& dup, bool& moved)
+{
+    const Lanes<16> sg;
+    const int pl = sg.pl;
+    const bool on = pl < act;
+    const uint32_t hd_max = sg.red_max(on ? __float_as_uint(pm) : 0u);
+    const uint32_t pen_min = sg.red_min(on ? __float_as_uint(__fadd_rn(pm, fabsf(lam))) : 0xffffffffu);
+    const bool fast = act == L && hd_max < pen_min;
+    if (__all_sync(0xffffffffu, fast || act == 0)) {
+        bitv = lam < 0.0f ? 1u : 0u;
+        dup = false;
+        moved = false;
+        return pl;
+    }
+    const int nc = 2 * act;
+    const float inf = __int_as_float(0x7f800000);
+    float cm0;
+    {
+        const float lp = sg.shfl(lam, (pl >> 1) & 15);
+        const float pp = sg.shfl(pm, (pl >> 1) & 15);
+        cm0 = ((uint32_t)(pl & 1) != (uint32_t)(lp < 0.0f)) ? __fadd_rn(pp, fabsf(lp)) : pp;
+        if (pl >= nc) cm0 = inf;
+    }
+    int rank0 = 0;
+    for (int c2 = 0; c2 < 2 * L; ++c2) {
+        const float o = sg.shfl(cm0, c2);
+        rank0 += (o < cm0) || (o == cm0 && c2 < pl);
+    }
+    const uint32_t below = (1u << pl) - 1u;
+    const uint32_t km0 = sg.ballot(pl < nc && (nc <= L || rank0 < L));
+    uint8_t* sel = selc + sg.base;
+    if (km0 & (1u << pl)) sel[__popc(km0 & below)] = (uint8_t)pl;
+    dup = (km0 & (km0 >> 1) & 0x55555555u) != 0u;
+    const int nact = __popc(km0);
+    __syncwarp();
+    const int cq = pl < nact ? sel[pl] : 0;
+    __syncwarp();
+    const float m0 = sg.shfl(cm0, cq & 15);
+    bitv = (uint32_t)(cq & 1);
+    pm = pl < nact ? m0 : 0.0f;
+    act = nact;
+    moved = __any_sync(0xffffffffu, pl < nact && (cq >> 1) != pl);
+    return cq >> 1;
+}
+
+// Decode one frame per list: the warp's frame (W = 32), or each half-warp's frame (W = 16; a
+// half without a frame passes frame < 0 and decodes nothing).  TWO: L = 32, two candidates per
+// lane.
+template <bool TWO, int W>
 __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, const SCLWarp& S, uint8_t* selc)
 {
-    const int lane = threadIdx.x & 31;
+    static_assert(W == 32 || !TWO, "half-warp lists hold at most 8 paths");
+    const Lanes<W> sg;
+    const int lane = sg.pl;  // path of this lane within its list
     const int N = C.N, n = C.n, L = a.L;
-    const float* y = a.llr + (a.llr_off ? a.llr_off[frame] : (long long)frame * N);
+    const float* y = a.llr + (frame < 0 ? 0 : (a.llr_off ? a.llr_off[frame] : (long long)frame * N));
     uint32_t pA[2] = {0u, 0u}, pC[2] = {0u, 0u};  // upper-level pointer rows of path `lane`
     float pm = 0.0f;
-    int act = 1;
+    int act = frame < 0 ? 0 : 1;
     uint32_t shA = 0u, shC = 0u;  // upper levels that may be shared since the last duplication
     Leaf lf;
 #pragma unroll
@@ -442,11 +575,12 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
         // ------------------------------------------------ upper levels on entering the block
         const int t = blk == 0 ? n : 5 + __ffs(blk) - 1;
         const int top = blk == 0 ? n - 1 : t;
+        const int act_both = sg.both_max(act);
         for (int k = top; k >= 5; --k) {
             // level 5 goes to the staging rows (indexed by path), levels >= 6 to their arrays
             const bool stage = k == 5;
-            if (!stage && ((shA >> k) & 1u)) {
-                scl_own(pA, k, act, L);
+            if (!stage && __any_sync(0xffffffffu, (shA >> k) & 1u)) {
+                scl_own<W>(pA, k, act, L);
                 shA &= ~(1u << k);
             }
             const bool use_g = blk != 0 && k == t;
@@ -458,20 +592,20 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             const uint32_t* cbk = S.Cl(k);
             const uint32_t my_d = stage ? (uint32_t)lane : fld(pA, k), my_s = from_ch ? 0u : fld(pA, k + 1),
                            my_c = fld(pC, k);
-            const int cwk = scl_cs(k), total = act << k;
+            const int cwk = scl_cs(k), total = act << k, tmax = act_both << k;
             // four elements per lane per round: all loads of a round are issued before any store,
             // so the L2 latency of the upper levels overlaps
-            for (int e0 = 0; e0 < total; e0 += 128) {
+            for (int e0 = 0; e0 < tmax; e0 += 4 * W) {
                 float va[4], vb[4];
                 uint32_t vw[4], pdv[4];
                 int jv[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int e = e0 + 32 * q + lane;
-                    const int p = (e >> k) & 31;
-                    pdv[q] = __shfl_sync(0xffffffffu, my_d, p);
-                    const uint32_t ps = __shfl_sync(0xffffffffu, my_s, p);
-                    const uint32_t pc = __shfl_sync(0xffffffffu, my_c, p);
+                    const int e = e0 + W * q + lane;
+                    const int p = (e >> k) & (W - 1);
+                    pdv[q] = sg.shfl(my_d, p);
+                    const uint32_t ps = sg.shfl(my_s, p);
+                    const uint32_t pc = sg.shfl(my_c, p);
                     jv[q] = e & (len - 1);
                     va[q] = vb[q] = 0.0f;
                     vw[q] = 0u;
@@ -484,7 +618,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int e = e0 + 32 * q + lane;
+                    const int e = e0 + W * q + lane;
                     if (e < total) {
                         const float r = use_g ? scl_g(va[q], vb[q], (vw[q] >> (jv[q] & 31)) & 1u) : xmin(va[q], vb[q]);
                         dst[pdv[q] * dstride + jv[q]] = r;
@@ -522,13 +656,17 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                 if (lane < act && lam < 0.0f) pm = __fadd_rn(pm, fabsf(lam));
             } else {
                 bool dup = false;
-                parent = scl_list_step<TWO>(lam, pm, act, L, selc, bitv, dup, moved);
+                if constexpr (W == 32)
+                    parent = scl_list_step<TWO>(lam, pm, act, L, selc, bitv, dup, moved);
+                else
+                    parent = scl_list_step_half(lam, pm, act, L, selc, bitv, dup, moved);
                 if (moved) {
-                    leaf_inherit_rt(lf, parent, leaf_live_mask(r));
-                    pA[0] = __shfl_sync(0xffffffffu, pA[0], parent);
-                    pA[1] = __shfl_sync(0xffffffffu, pA[1], parent);
-                    pC[0] = __shfl_sync(0xffffffffu, pC[0], parent);
-                    pC[1] = __shfl_sync(0xffffffffu, pC[1], parent);
+                    const int src = sg.base + parent;
+                    leaf_inherit_rt(lf, src, leaf_live_mask(r));
+                    pA[0] = __shfl_sync(0xffffffffu, pA[0], src);
+                    pA[1] = __shfl_sync(0xffffffffu, pA[1], src);
+                    pC[0] = __shfl_sync(0xffffffffu, pC[0], src);
+                    pC[1] = __shfl_sync(0xffffffffu, pC[1], src);
                 }
                 if (dup) shA = shC = 0xffffffffu;
             }
@@ -543,8 +681,8 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
         {
             const int i_last = blk * 32 + 31;
             const int kc = __ffs(~i_last) - 1;  // >= 5; n after the last block
-            if ((shC >> kc) & 1u) {
-                scl_own(pC, kc, act, L);
+            if (__any_sync(0xffffffffu, (shC >> kc) & 1u)) {
+                scl_own<W>(pC, kc, act, L);
                 shC &= ~(1u << kc);
             }
             uint32_t* dstl = S.Cl(kc);
@@ -552,20 +690,21 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             if (lane < act) dstl[fld(pC, kc) * cwk] = v5;
             __syncwarp();
             const uint32_t my_dst = fld(pC, kc);
+            const int act_both2 = sg.both_max(act);
             for (int k = 5; k < kc; ++k) {
-                const int W = 1 << (k - 5), total = act * W;
+                const int Wk = 1 << (k - 5), total = act * Wk, tmax = act_both2 * Wk;
                 const uint32_t* ckb = S.Cl(k);
                 const uint32_t my_k = fld(pC, k);
-                for (int e0 = 0; e0 < total; e0 += 32) {
+                for (int e0 = 0; e0 < tmax; e0 += W) {
                     const int e = e0 + lane;
-                    const int p = (e / W) & 31;
-                    const uint32_t pd = __shfl_sync(0xffffffffu, my_dst, p);
-                    const uint32_t pk = __shfl_sync(0xffffffffu, my_k, p);
+                    const int p = (e / Wk) & (W - 1);
+                    const uint32_t pd = sg.shfl(my_dst, p);
+                    const uint32_t pk = sg.shfl(my_k, p);
                     if (e < total) {
-                        const int w = e % W;
+                        const int w = e % Wk;
                         uint32_t* dst = dstl + pd * cwk;
                         const uint32_t x = dst[w];
-                        dst[W + w] = x;
+                        dst[Wk + w] = x;
                         dst[w] = x ^ ckb[pk * scl_cs(k) + w];
                     }
                 }
@@ -575,35 +714,42 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
     }
     // ------------------------------------------------------------------ CRC selection
     // u = x G on each path's N-bit codeword (level-n array), in place; syndrome of its
-    // information bits
+    // information bits.  The list's lanes hold the codeword's 32-bit words lane + W h.
+    constexpr int H = 64 / W;  // words per lane for N <= 2048
     const int words = N >> 5;
     uint32_t* xl = S.Cl(n);
     const uint32_t my_x = fld(pC, n);
     uint32_t synd = 0xffffffffu;  // lane p: syndrome of path p
-    for (int p = 0; p < act; ++p) {
-        uint32_t* xw = xl + __shfl_sync(0xffffffffu, my_x, p) * scl_cs(n);
-        uint32_t w[2] = {0u, 0u};
+    const int act_both = sg.both_max(act);
+    for (int p = 0; p < act_both; ++p) {
+        const bool live = p < act;
+        uint32_t* xw = xl + sg.shfl(my_x, p) * scl_cs(n);
+        uint32_t w[H];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-            if (lane + 32 * h < words) w[h] = xw[lane + 32 * h];
+        for (int h = 0; h < H; ++h) w[h] = (live && lane + W * h < words) ? xw[lane + W * h] : 0u;
         const uint32_t m[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < H; ++h)
 #pragma unroll
             for (int e = 0; e < 5; ++e) w[h] ^= (w[h] >> (1 << e)) & m[e];
-        for (int D = 1; D < 32 && D < words; D <<= 1) {
+        for (int D = 1; D < W && D < words; D <<= 1) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < H; ++h) {
                 const uint32_t o = __shfl_xor_sync(0xffffffffu, w[h], D);
                 if (!(lane & D)) w[h] ^= o;
             }
         }
-        if (words > 32) w[0] ^= w[1];
+        for (int D = W; D < words; D <<= 1) {
+            const int hd = D / W;
+#pragma unroll
+            for (int h = 0; h < H; ++h)
+                if (!(h & hd) && (h | hd) < H) w[h] ^= w[h | hd];
+        }
         uint32_t s = 0u;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int wi = lane + 32 * h;
-            if (wi < words) {
+        for (int h = 0; h < H; ++h) {
+            const int wi = lane + W * h;
+            if (live && wi < words) {
                 xw[wi] = w[h];
                 uint32_t bitsw = w[h];
                 while (bitsw) {
@@ -613,18 +759,18 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                 }
             }
         }
-        s = __reduce_xor_sync(0xffffffffu, s);
+        s = sg.red_xor(s);
         if (lane == p) synd = s;
     }
     __syncwarp();
     // first CRC-passing path in (metric, index) order, else the best metric
     const bool ok_lane = lane < act && synd == 0u;
-    const bool any_ok = __ballot_sync(0xffffffffu, ok_lane) != 0u;
+    const bool any_ok = sg.ballot(ok_lane) != 0u;
     const bool cand = any_ok ? ok_lane : lane < act;
     float key = cand ? pm : __int_as_float(0x7f800000);
     int who = cand ? lane : 64;
 #pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
+    for (int off = W / 2; off >= 1; off >>= 1) {
         const float ok2 = __shfl_xor_sync(0xffffffffu, key, off);
         const int ow = __shfl_xor_sync(0xffffffffu, who, off);
         if (ok2 < key || (ok2 == key && ow < who)) {
@@ -632,55 +778,72 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             who = ow;
         }
     }
-    const uint32_t* uw = xl + __shfl_sync(0xffffffffu, my_x, who & 31) * scl_cs(n);
-    uint8_t* out = a.bits + (size_t)frame * a.row_bytes;
-    for (int by = lane; by < a.row_bytes; by += 32) {
-        uint32_t v = 0u;
-        for (int r = 0; r < 8; ++r) {
-            const int p = by * 8 + r;
-            if (p >= C.P) break;
-            const int j = C.info_idx[p];
-            v |= ((uw[j >> 5] >> (j & 31)) & 1u) << r;
+    const uint32_t* uw = xl + sg.shfl(my_x, who & (W - 1)) * scl_cs(n);
+    if (frame >= 0) {
+        uint8_t* out = a.bits + (size_t)frame * a.row_bytes;
+        for (int by = lane; by < a.row_bytes; by += W) {
+            uint32_t v = 0u;
+            for (int r = 0; r < 8; ++r) {
+                const int p = by * 8 + r;
+                if (p >= C.P) break;
+                const int j = C.info_idx[p];
+                v |= ((uw[j >> 5] >> (j & 31)) & 1u) << r;
+            }
+            out[by] = (uint8_t)v;
         }
-        out[by] = (uint8_t)v;
+        if (lane == 0) a.status[frame] = any_ok ? POLAR_FRAME_SCL_OK : POLAR_FRAME_SCL_CRC_FAIL;
     }
-    if (lane == 0) a.status[frame] = any_ok ? POLAR_FRAME_SCL_OK : POLAR_FRAME_SCL_CRC_FAIL;
     __syncwarp();
 }
 
-template <bool TWO>
+// Decode `frame` (frame < 0: nothing, on this lane's list) by the calling warp: plan of its code,
+// the list's shared words `ws` and global slot `slot` (null: every level in shared memory).
+template <bool TWO, int W>
+__device__ __forceinline__ void scl_warp_frame(const SCLArgs& a, int frame, uint32_t* ws, float* slot, uint8_t* selc)
+{
+    const int L = a.L;
+    const DevCode& C = (a.code_of && frame >= 0) ? *a.codes[a.code_of[frame]] : *a.code;
+    SCLWarp S;
+    S.L = L;
+    if (a.code_of) {
+        const SCLPlan p = scl_plan(C.N, L, slot == nullptr);
+        S.KS = p.KS;
+        S.KC = p.KC;
+    } else {
+        S.KS = a.KS;
+        S.KC = a.KC;
+    }
+    S.sC = ws;
+    S.sA = reinterpret_cast<float*>(ws + scl_smem_c_words(S.KC, L));
+    S.stage = S.sA + scl_smem_llr_words(S.KS, L);
+    S.gA = slot;
+    S.gC = slot ? reinterpret_cast<uint32_t*>(slot + (size_t)L * (C.N - (2 << S.KS))) : nullptr;
+    scl_decode_frame<TWO, W>(a, C, frame, S, selc);
+}
+
+// W = 32: one frame per warp; W = 16: two (one per half-warp list), claimed together.
+template <bool TWO, int W>
 __global__ void __launch_bounds__(kSclWarpsPerCTA * 32) scl_kernel(const SCLArgs a)
 {
+    constexpr int LISTS = 32 / W;
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int L = a.L;
-    uint32_t* ws = smem + (size_t)wid * a.warp_words;
-    uint8_t* selc = reinterpret_cast<uint8_t*>(ws + a.warp_words - 16);
-    float* slot = a.scratch ? a.scratch + ((size_t)blockIdx.x * (blockDim.x >> 5) + wid) * (size_t)a.slot_words : nullptr;
+    const int li = lane / W;  // this lane's list
+    uint32_t* wsw = smem + (size_t)wid * a.warp_words;
+    uint32_t* ws = wsw + li * a.list_words;
+    uint8_t* selc = reinterpret_cast<uint8_t*>(wsw + a.warp_words - 16);
+    float* slot = a.scratch
+        ? a.scratch + (((size_t)blockIdx.x * (blockDim.x >> 5) + wid) * LISTS + li) * (size_t)a.slot_words
+        : nullptr;
     const int count = a.count ? *a.count : a.B;
     for (;;) {
         int idx = 0;
-        if (lane == 0) idx = atomicAdd(a.next, 1);
+        if (lane == 0) idx = atomicAdd(a.next, LISTS);
         idx = __shfl_sync(0xffffffffu, idx, 0);
-        if (idx >= count) break;
-        const int frame = a.list ? a.list[idx] : idx;
-        const DevCode& C = a.code_of ? *a.codes[a.code_of[frame]] : *a.code;
-        SCLWarp S;
-        S.L = L;
-        if (a.code_of) {
-            const SCLPlan p = scl_plan(C.N, L, slot == nullptr);
-            S.KS = p.KS;
-            S.KC = p.KC;
-        } else {
-            S.KS = a.KS;
-            S.KC = a.KC;
-        }
-        S.sC = ws;
-        S.sA = reinterpret_cast<float*>(ws + scl_smem_c_words(S.KC, L));
-        S.stage = S.sA + scl_smem_llr_words(S.KS, L);
-        S.gA = slot;
-        S.gC = slot ? reinterpret_cast<uint32_t*>(slot + (size_t)L * (C.N - (2 << S.KS))) : nullptr;
-        scl_decode_frame<TWO>(a, C, frame, S, selc);
+        if (idx >= count) break;  // uniform over the warp
+        const int k = idx + li;
+        const int frame = k < count ? (a.list ? a.list[k] : k) : -1;
+        scl_warp_frame<TWO, W>(a, frame, ws, slot, selc);
     }
 }
 
@@ -689,18 +852,20 @@ __global__ void __launch_bounds__(kSclWarpsPerCTA * 32) scl_kernel(const SCLArgs
 cudaError_t scl_launch(SCLArgs a, int N, int L, cudaStream_t st, int warp_words_max, long long slot_words_max)
 {
     const bool all_smem = a.scratch == nullptr;
-    const SCLPlan p = scl_plan(N, L, all_smem);
+    const int lists = scl_two_lists(L, all_smem, a.code_of == nullptr) ? 2 : 1;
+    const SCLPlan p = scl_plan(N, L, all_smem, lists);
     a.KS = p.KS;
     a.KC = p.KC;
-    a.warp_words = std::max(p.warp_words, warp_words_max);
+    a.list_words = std::max(p.list_words, warp_words_max - 16);
+    a.warp_words = lists * a.list_words + 16;
     a.slot_words = std::max(p.slot_words, slot_words_max);
-    const SCLPlan pw = {p.KS, p.KC, a.warp_words, a.slot_words};
     int W = kSclWarpsPerCTA;
-    const size_t wb = (size_t)pw.warp_words * 4;
+    const size_t wb = (size_t)a.warp_words * 4;
     while (W > 1 && (size_t)W * wb > 200 * 1024) W >>= 1;
     const size_t smem = (size_t)W * wb;
     const bool two = L > 16;
-    const void* fn = two ? (const void*)scl_kernel<true> : (const void*)scl_kernel<false>;
+    const void* fn = lists == 2 ? (const void*)scl_kernel<false, 16>
+                                : (two ? (const void*)scl_kernel<true, 32> : (const void*)scl_kernel<false, 32>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -709,13 +874,15 @@ cudaError_t scl_launch(SCLArgs a, int N, int L, cudaStream_t st, int warp_words_
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int sms = scl_sm_count();
     long long grid = (long long)sms * per_sm;
-    if (!all_smem) grid = std::min<long long>(grid, (long long)sms * kSclWarpsPerSM / W);
-    if (!a.list) grid = std::min<long long>(grid, (a.B + W - 1) / W);
+    if (!all_smem) grid = std::min<long long>(grid, (long long)sms * kSclWarpsPerSM / (W * lists));
+    if (!a.list) grid = std::min<long long>(grid, (a.B + W * lists - 1) / (W * lists));
     if (grid < 1) grid = 1;
-    if (two)
-        scl_kernel<true><<<(unsigned)grid, W * 32, smem, st>>>(a);
+    if (lists == 2)
+        scl_kernel<false, 16><<<(unsigned)grid, W * 32, smem, st>>>(a);
+    else if (two)
+        scl_kernel<true, 32><<<(unsigned)grid, W * 32, smem, st>>>(a);
     else
-        scl_kernel<false><<<(unsigned)grid, W * 32, smem, st>>>(a);
+        scl_kernel<false, 32><<<(unsigned)grid, W * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
