@@ -17,6 +17,7 @@ import os
 import subprocess
 import threading
 from dataclasses import dataclass
+from typing import Optional
 
 import numpy as np
 
@@ -91,13 +92,18 @@ def _declare(L):
         getattr(L, "or_sc_bit_llr_" + sfx).argtypes = [_f32p, _c_int, _u8p, _c_int]
         getattr(L, "or_sc_bit_llr_" + sfx).restype = _c_double
         getattr(L, "or_scl_decode_" + sfx).argtypes = [
-            _f32p, _c_int, _u8p, _i32p, _c_int, _c_uint, _c_int, _c_int, _u8p, _f64p, _u8p, _f64p,
+            _f32p, _c_int, _u8p, _u8p, _i32p, _c_int, _c_uint, _c_int, _c_int, _u8p, _f64p, _u8p, _f64p,
             _i32p]
         getattr(L, "or_scl_decode_batch_" + sfx).argtypes = [
-            _f32p, _c_int, _c_int, _u8p, _i32p, _c_int, _c_uint, _c_int, _c_int, _u8p, _u8p, _f64p]
+            _f32p, _c_int, _c_int, _u8p, _u8p, _i32p, _c_int, _c_uint, _c_int, _c_int, _u8p, _u8p, _f64p]
         getattr(L, "or_hybrid_decode_batch_" + sfx).argtypes = [
-            _f32p, _c_int, _c_int, _u8p, _i32p, _c_int, _c_uint, _c_int, _c_int, _c_double, _c_int,
+            _f32p, _c_int, _c_int, _u8p, _u8p, _i32p, _c_int, _c_uint, _c_int, _c_int, _c_double, _c_int,
             _f32p, _c_int, _u8p, _u8p, _i32p]
+
+
+def _dec(code):
+    """The decision-aided mask of a code as a contiguous uint8 array, or None."""
+    return None if code.decided is None else np.ascontiguousarray(code.decided, dtype=np.uint8)
 
 
 def _p(a, t):
@@ -121,6 +127,8 @@ class Code:
     crc_poly: int
     frozen: np.ndarray    # uint8 [N], 1 = frozen
     info_idx: np.ndarray  # int32 [K], ascending
+    # uint8 [N] or None: information positions CA-SCL decides without branching (decision aiding)
+    decided: Optional[np.ndarray] = None
 
     @property
     def n(self) -> int:
@@ -309,7 +317,7 @@ def scl_decode(llr, code: Code, L: int, precision: str = "f32") -> dict:
     st = np.zeros(B, np.uint8)
     pm = np.zeros(B, np.float64)
     getattr(lib(), "or_scl_decode_batch_" + precision)(
-        _p(llr, _f32p), B, N, _p(code.frozen, _u8p), _p(code.info_idx, _i32p), code.K,
+        _p(llr, _f32p), B, N, _p(code.frozen, _u8p), _p(_dec(code), _u8p), _p(code.info_idx, _i32p), code.K,
         code.crc_poly, code.crc_len, L, _p(u, _u8p), _p(st, _u8p), _p(pm, _f64p))
     return {"u_hat": u, "status": st, "pm": pm}
 
@@ -323,7 +331,7 @@ def scl_list(llr_row, code: Code, L: int, precision: str = "f32"):
     pm = np.zeros(1, np.float64)
     na = np.zeros(1, np.int32)
     ok = getattr(lib(), "or_scl_decode_" + precision)(
-        _p(row, _f32p), code.N, _p(code.frozen, _u8p), _p(code.info_idx, _i32p), code.K,
+        _p(row, _f32p), code.N, _p(code.frozen, _u8p), _p(_dec(code), _u8p), _p(code.info_idx, _i32p), code.K,
         code.crc_poly, code.crc_len, L, _p(u, _u8p), _p(pm, _f64p), _p(lu, _u8p), _p(lpm, _f64p),
         _p(na, _i32p))
     a = int(na[0])
@@ -343,7 +351,7 @@ def hybrid_decode(llr, code: Code, max_iters: int, llr_max: float, L: int, w=Non
         w = _f32(w)
         w_iters = w.shape[0]
     getattr(lib(), "or_hybrid_decode_batch_" + precision)(
-        _p(llr, _f32p), B, N, _p(code.frozen, _u8p), _p(code.info_idx, _i32p), code.K,
+        _p(llr, _f32p), B, N, _p(code.frozen, _u8p), _p(_dec(code), _u8p), _p(code.info_idx, _i32p), code.K,
         code.crc_poly, code.crc_len, max_iters, llr_max, L, _p(w, _f32p), w_iters, _p(u, _u8p),
         _p(st, _u8p), _p(it, _i32p))
     return {"u_hat": u, "status": st, "iters": it}

@@ -435,3 +435,54 @@ def test_wms_gradient_all_iterations_matches_central_differences(N, T):
         wm.flat[i] -= h
         fd = (f(wp) - f(wm)) / (float(wp.flat[i]) - float(wm.flat[i]))
         assert fd == pytest.approx(g.flat[i], rel=1e-6, abs=1e-9), i
+
+
+# ---------------------------------------------------------------------------- decision aiding
+def _da_code(N, K, crc, frac, seed):
+    """The code with a random subset (fraction `frac`) of its information positions decided."""
+    import dataclasses
+    code = oracle.make_code(N, K, crc)
+    rng = np.random.default_rng(seed)
+    dec = np.zeros(N, np.uint8)
+    pick = rng.choice(code.info_idx, int(frac * K), replace=False)
+    dec[pick] = 1
+    return dataclasses.replace(code, decided=dec)
+
+
+@pytest.mark.parametrize("N,K,crc", [(64, 32, 8), (128, 64, 8)])
+def test_decision_aided_list_of_one_is_sc(N, K, crc):
+    """With L = 1 the list never branches, so deciding some positions by the hard decision (what
+    SC does at every information position) changes nothing: CA-SCL(L = 1) = SC for any mask."""
+    code = _da_code(N, K, crc, 0.5, N)
+    rng = np.random.default_rng(N + 1)
+    llr = rng.normal(1.0, 2.5, (20, N)).astype(np.float32)
+    sc = oracle.sc_decode(llr, code)
+    assert np.array_equal(oracle.scl_decode(llr, code, 1)["u_hat"], sc)
+
+
+@pytest.mark.parametrize("L", [2, 4, 8])
+def test_decision_aided_all_information_bits_is_sc(L):
+    """Every information position decided: the list never grows past one path, for any L."""
+    import dataclasses
+    code = oracle.make_code(128, 64, 8)
+    dec = (1 - code.frozen).astype(np.uint8)
+    code = dataclasses.replace(code, decided=dec)
+    rng = np.random.default_rng(L)
+    llr = rng.normal(1.0, 2.5, (20, 128)).astype(np.float32)
+    assert np.array_equal(oracle.scl_decode(llr, code, L)["u_hat"], oracle.sc_decode(llr, code))
+
+
+def test_decision_aided_empty_mask_is_plain_and_noiseless_decodes():
+    import dataclasses
+    plain = oracle.make_code(128, 64, 8)
+    empty = dataclasses.replace(plain, decided=np.zeros(128, np.uint8))
+    rng = np.random.default_rng(9)
+    llr = rng.normal(1.0, 2.5, (30, 128)).astype(np.float32)
+    a, b = oracle.scl_decode(llr, plain, 4), oracle.scl_decode(llr, empty, 4)
+    assert np.array_equal(a["u_hat"], b["u_hat"]) and np.array_equal(a["status"], b["status"])
+    code = _da_code(128, 64, 8, 0.5, 3)
+    pay = rng.integers(0, 2, (10, code.P)).astype(np.uint8)
+    x = oracle.encode_batch(pay, code)
+    out = oracle.scl_decode(20.0 * (1.0 - 2.0 * x.astype(np.float32)), code, 4)
+    assert np.array_equal(oracle.payload_of(out["u_hat"], code), pay)
+    assert (out["status"] == 2).all()
