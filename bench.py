@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--da-bits", type=int, default=128,
+                    help="decision-aided block: information positions CA-SCL decides without branching")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1609_09358_gb300", "weights", "wms_n1024_k512_t20.pt"))
     return ap.parse_args()
 
@@ -324,6 +326,8 @@ def main():
 
     if prec == api.POLAR_FP32 and not a.no_learned:
         line["plain_fp16"] = plain_fp16(a, code, llr, payload, stream, dist)
+        if a.da_bits > 0:
+            line["decision_aided"] = decision_aided(a, code, llr, payload, stream, dist)
     if not a.no_learned and os.path.exists(a.weights):
         line["learned_fp16"] = learned(a, llr, payload, stream, dist)
         line["learned_fp16_imax%d" % IMAX] = learned(a, llr, payload, stream, dist, IMAX)
@@ -339,6 +343,47 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def decision_aided(a, code, llr, payload, stream, dist):
+    """Decision-aided CA-SCL (Sec. II-A) on the same frames: the da_bits most reliable information
+    positions (Bhattacharyya at the construction's design point) are decided by each path's hard
+    decision without branching the list; FP32 BP as in the main line."""
+    import torch
+
+    from paper_1609_09358_gb300 import api
+    mask = api.decided_mask(code, a.da_bits)
+    dcode = api.PolarCode(code.N, code.K, code.crc_len, code.frozen, code.crc_poly, decided=mask)
+    B = llr.shape[0]
+    dec = api.Decoder(dcode, B, LIST, device=llr.device)
+
+    def step():
+        dec.hybrid(llr, IMAX, LLR_MAX, api.POLAR_FP32)
+
+    for _ in range(max(a.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    steps = max(1, min(a.steps, 50))
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    api.polar_profile_enable(True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    api.polar_profile_enable(False)
+    bp_ms, _, scl_ms, _ = api.polar_profile_read()
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=llr.device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    world = dist.get_world_size() if dist else 1
+    ferr = (dec.bits != payload).any(dim=1)
+    return {"value": world * code.P * B * steps / (float(t.item()) * 1e-3) / 1e9, "unit": "Gbit/s", "steps": steps,
+            "ms_per_step": float(t.item()) / steps, "fer": float(ferr.float().mean().item()),
+            "fallback_rate": float((dec.status != api.FRAME_BP_OK).float().mean().item()),
+            "da_bits": a.da_bits, "bp_ms_per_step": bp_ms / steps, "scl_ms_per_step": scl_ms / steps, "dtype": "f32"}
 
 
 def plain_fp16(a, code, llr, payload, stream, dist):

@@ -65,14 +65,18 @@ extern "C" {
 
 /* A polar code.  N = 2^n with POLAR_MIN_N <= N <= POLAR_MAX_N; K non-frozen positions of which
  * crc_len (0, 8, 16 or 24) carry the CRC, crc_len <= K <= N; frozen: HOST pointer to N bytes,
- * 1 = frozen (value 0), 0 = information.  The struct and the table are read during the call
- * only. */
+ * 1 = frozen (value 0), 0 = information.  scl_decided: NULL, or a HOST pointer to N bytes, 1 on
+ * information positions that CA-SCL decides by each path's hard decision without branching the
+ * list (the decision aiding of Sec. II-A, meant for the most reliable positions: see
+ * polar_reliability); it changes scl_decode and the CA-SCL stage of the hybrid decoders, not BP.
+ * The struct and the tables are read during the call only. */
 typedef struct polar_code {
     int32_t N;
     int32_t K;
     int32_t crc_len;
     uint32_t crc_poly;
     const uint8_t* frozen;
+    const uint8_t* scl_decided;
 } polar_code;
 
 /* Frozen-set construction (Sec. II: information on the K most reliable bit-channels; Sec. II-A
@@ -84,6 +88,12 @@ typedef struct polar_code {
  * design_rate <= 0. */
 int polar_construct(int32_t N, int32_t K, double design_ebn0_db, double design_rate,
                     uint8_t* frozen_out, int32_t* info_idx_out);
+
+/* Bhattacharyya parameters of the construction (Sec. II-A): ln Z of every bit-channel at the
+ * design point, computed as in polar_construct (smaller = more reliable).  Host only.
+ *   lnz_out: host, N doubles.  POLAR_ERR_ARG for N not a power of two in [2, 2^20], a bad design
+ *   point or a NULL output. */
+int polar_reliability(int32_t N, double design_ebn0_db, double design_rate, double* lnz_out);
 
 /* Systematic CRC + polar encoder (Sec. II, x = u G; CRC-aided construction of Sec. II-A).
  * payload: device, [B][ceil(P/8)] packed payload bits; codeword: device, [B][N/8] packed code

@@ -31,7 +31,8 @@ class PolarError(RuntimeError):
 
 class _PolarCode(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("K", ctypes.c_int32), ("crc_len", ctypes.c_int32),
-                ("crc_poly", ctypes.c_uint32), ("frozen", ctypes.POINTER(ctypes.c_uint8))]
+                ("crc_poly", ctypes.c_uint32), ("frozen", ctypes.POINTER(ctypes.c_uint8)),
+                ("scl_decided", ctypes.POINTER(ctypes.c_uint8))]
 
 
 _vp, _i32, _u64, _f32, _f64, _sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_float,
@@ -41,6 +42,7 @@ _CP = ctypes.POINTER(_PolarCode)
 # name -> (restype, argtypes); every exported symbol of the header
 SIGNATURES = {
     "polar_construct": (ctypes.c_int, [_i32, _i32, _f64, _f64, _vp, _vp]),
+    "polar_reliability": (ctypes.c_int, [_i32, _f64, _f64, _vp]),
     "polar_encode": (ctypes.c_int, [_CP, _vp, _i32, _vp, _vp]),
     "polar_random_payload": (ctypes.c_int, [_i32, _i32, _u64, _u64, _vp, _vp]),
     "polar_awgn_llr": (ctypes.c_int, [_vp, _i32, _i32, _f32, _vp, _u64, _u64, _vp, _vp]),
@@ -110,20 +112,25 @@ def _stream(stream=None) -> int:
 
 @dataclass
 class PolarCode:
-    """Host description of a code; `frozen` is uint8 [N] (1 = frozen)."""
+    """Host description of a code; `frozen` is uint8 [N] (1 = frozen); `decided` is None or uint8
+    [N], 1 on the information positions CA-SCL decides without branching (decision aiding)."""
     N: int
     K: int
     crc_len: int
     frozen: np.ndarray
     crc_poly: int = -1
+    decided: np.ndarray = None
     _c: _PolarCode = field(default=None, repr=False)
 
     def __post_init__(self):
         if self.crc_poly < 0:
             self.crc_poly = CRC_POLYS[self.crc_len]
         self.frozen = np.ascontiguousarray(self.frozen, dtype=np.uint8)
-        self._c = _PolarCode(self.N, self.K, self.crc_len, self.crc_poly,
-                             self.frozen.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        if self.decided is not None:
+            self.decided = np.ascontiguousarray(self.decided, dtype=np.uint8)
+        self._c = _PolarCode(self.N, self.K, self.crc_len, self.crc_poly, self.frozen.ctypes.data_as(u8p),
+                             self.decided.ctypes.data_as(u8p) if self.decided is not None else None)
 
     @property
     def P(self) -> int:
@@ -151,6 +158,27 @@ def polar_construct(N: int, K: int, design_ebn0_db: float, design_rate: float):
     _check(load().polar_construct(N, K, design_ebn0_db, design_rate, frozen.ctypes.data, info.ctypes.data),
            "polar_construct")
     return frozen, info[:K]
+
+
+def polar_reliability(N: int, design_ebn0_db: float, design_rate: float) -> np.ndarray:
+    """ln Z of every bit-channel at the design point (smaller = more reliable)."""
+    lnz = np.zeros(N, np.float64)
+    _check(load().polar_reliability(N, design_ebn0_db, design_rate, lnz.ctypes.data), "polar_reliability")
+    return lnz
+
+
+def decided_mask(code: PolarCode, count: int, design_ebn0_db: float = 0.0, design_rate=None) -> np.ndarray:
+    """uint8 [N]: the `count` most reliable information positions (smallest ln Z at the design
+    point; ties: the larger index, as in the construction) -- CA-SCL decides them without
+    branching."""
+    if design_rate is None:
+        design_rate = code.P / code.N
+    lnz = polar_reliability(code.N, design_ebn0_db, design_rate)
+    info = code.info_idx
+    order = sorted(info.tolist(), key=lambda i: (lnz[i], -i))
+    mask = np.zeros(code.N, np.uint8)
+    mask[order[:count]] = 1
+    return mask
 
 
 def make_code(N: int, K: int, crc_len: int, design_ebn0_db: float = 0.0, design_rate=None) -> PolarCode:

@@ -76,6 +76,10 @@ static int check_code(const polar_code* code)
     int info = 0;
     for (int i = 0; i < N; ++i) info += code->frozen[i] ? 0 : 1;
     if (info != K) return fail(POLAR_ERR_ARG, "frozen table has %d information positions, K = %d", info, K);
+    if (code->scl_decided)
+        for (int i = 0; i < N; ++i)
+            if (code->scl_decided[i] && code->frozen[i])
+                return fail(POLAR_ERR_ARG, "scl_decided marks the frozen position %d", i);
     return POLAR_OK;
 }
 
@@ -97,6 +101,7 @@ static void derive_code(const polar_code* code, DevCode& d)
             d.frozen_bits[i >> 5] |= 1u << (i & 31);
         else
             info.push_back(i);
+        if (code->scl_decided && code->scl_decided[i]) d.decided_bits[i >> 5] |= 1u << (i & 31);
     }
     // powers x^m mod g(x), m = 0..K-1, by repeated multiplication with x
     std::vector<uint32_t> pw(d.K > 0 ? d.K : 1);
@@ -390,26 +395,12 @@ static int launch_scl(const DevCode* dcode, const polar_code* code, const float*
     return e == cudaSuccess ? POLAR_OK : cuda_fail(e, "scl_kernel launch");
 }
 
-}  // namespace polar
-
-using namespace polar;
-
-// ==================================================================================== C ABI
-extern "C" {
-
-const char* polar_last_error(void) { return g_last_error.c_str(); }
-
-int polar_construct(int32_t N, int32_t K, double design_ebn0_db, double design_rate, uint8_t* frozen_out,
-                    int32_t* info_idx_out)
+// ln Z of every bit-channel, one combining level at a time: each level splits every channel into
+// its minus (index bit 0) and plus (index bit 1) child, so the first level decides the index MSB.
+// minus: ln(2Z - Z^2), plus: 2 ln Z.
+static std::vector<double> bhattacharyya_lnz(int N, double design_ebn0_db, double design_rate)
 {
-    if (!is_pow2(N) || N < 2 || N > (1 << 20)) return fail(POLAR_ERR_ARG, "N = %d: power of two in [2, 2^20]", N);
-    if (K < 0 || K > N) return fail(POLAR_ERR_ARG, "K = %d outside [0, N]", K);
-    if (!(design_rate > 0.0) || !std::isfinite(design_ebn0_db)) return fail(POLAR_ERR_ARG, "bad design point");
-    if (!frozen_out) return fail(POLAR_ERR_ARG, "frozen_out is NULL");
     const int n = log2i(N);
-    // ln Z of every bit-channel, one combining level at a time: each level splits every channel
-    // into its minus (index bit 0) and plus (index bit 1) child, so the first level decides the
-    // index MSB.  minus: ln(2Z - Z^2), plus: 2 ln Z.
     std::vector<double> lz(1, -design_rate * std::pow(10.0, design_ebn0_db / 10.0)), next;
     for (int level = 0; level < n; ++level) {
         next.resize(lz.size() * 2);
@@ -427,6 +418,36 @@ int polar_construct(int32_t N, int32_t K, double design_ebn0_db, double design_r
         }
         lz.swap(next);
     }
+    return lz;
+}
+
+}  // namespace polar
+
+using namespace polar;
+
+// ==================================================================================== C ABI
+extern "C" {
+
+const char* polar_last_error(void) { return g_last_error.c_str(); }
+
+int polar_reliability(int32_t N, double design_ebn0_db, double design_rate, double* lnz_out)
+{
+    if (!is_pow2(N) || N < 2 || N > (1 << 20)) return fail(POLAR_ERR_ARG, "N = %d: power of two in [2, 2^20]", N);
+    if (!(design_rate > 0.0) || !std::isfinite(design_ebn0_db)) return fail(POLAR_ERR_ARG, "bad design point");
+    if (!lnz_out) return fail(POLAR_ERR_ARG, "lnz_out is NULL");
+    const std::vector<double> lz = bhattacharyya_lnz(N, design_ebn0_db, design_rate);
+    for (int i = 0; i < N; ++i) lnz_out[i] = lz[i];
+    return POLAR_OK;
+}
+
+int polar_construct(int32_t N, int32_t K, double design_ebn0_db, double design_rate, uint8_t* frozen_out,
+                    int32_t* info_idx_out)
+{
+    if (!is_pow2(N) || N < 2 || N > (1 << 20)) return fail(POLAR_ERR_ARG, "N = %d: power of two in [2, 2^20]", N);
+    if (K < 0 || K > N) return fail(POLAR_ERR_ARG, "K = %d outside [0, N]", K);
+    if (!(design_rate > 0.0) || !std::isfinite(design_ebn0_db)) return fail(POLAR_ERR_ARG, "bad design point");
+    if (!frozen_out) return fail(POLAR_ERR_ARG, "frozen_out is NULL");
+    const std::vector<double> lz = bhattacharyya_lnz(N, design_ebn0_db, design_rate);
     std::vector<int> order(N);
     for (int i = 0; i < N; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {

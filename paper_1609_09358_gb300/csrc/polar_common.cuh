@@ -19,6 +19,7 @@ struct DevCode {
     int32_t N, n, K, P, c;
     uint32_t poly;
     uint32_t frozen_bits[kMaxWords];  // bit i of word i/32 set = node i frozen
+    uint32_t decided_bits[kMaxWords]; // information positions CA-SCL decides without branching
     // Syndrome column of node i: x^(K-1-k) mod g(x) for the node's information index k, 0 for a
     // frozen node.  The XOR of the columns of the information nodes decided 1 is the remainder of
     // the decided K-bit word divided by g(x): zero iff the CRC holds.

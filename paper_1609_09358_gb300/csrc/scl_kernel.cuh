@@ -638,7 +638,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
         // A runtime loop: one copy of the list step serves all 32 bits, and only the per-bit leaf
         // code (whose register indices are compile-time constants) is dispatched by the bit index.
         // Unrolling the block with a list step inlined per bit overflowed the instruction cache.
-        const uint32_t fw = C.frozen_bits[blk];
+        const uint32_t fw = C.frozen_bits[blk], dw = C.decided_bits[blk];
         uint32_t v5 = 0u;
 #pragma unroll 1
         for (int r = 0; r < 32; ++r) {
@@ -654,6 +654,9 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             int parent = lane;
             if ((fw >> r) & 1u) {
                 if (lane < act && lam < 0.0f) pm = __fadd_rn(pm, fabsf(lam));
+            } else if ((dw >> r) & 1u) {
+                // decision aiding: each path takes its hard decision, no branching, no metric
+                bitv = lam < 0.0f ? 1u : 0u;
             } else {
                 bool dup = false;
                 if constexpr (W == 32)

@@ -69,3 +69,32 @@ def test_bit_packing_roundtrip():
     rng = np.random.default_rng(0)
     b = rng.integers(0, 2, (5, 61), dtype=np.uint8)
     assert np.array_equal(api.unpack_bits(api.pack_bits(b), 61), b)
+
+
+@pytest.mark.parametrize("N,design_db,rate", [(64, 0.0, 0.5), (1024, 1.0, 0.484375), (2048, -1.0, 0.25)])
+def test_reliability_matches_oracle_and_construction(lib, N, design_db, rate):
+    """polar_reliability equals the oracle's Bhattacharyya recursion and orders the channels as
+    polar_construct does (its K most reliable are the information set)."""
+    lnz = api.polar_reliability(N, design_db, rate)
+    lnz0 = -rate * 10 ** (design_db / 10)
+    n = N.bit_length() - 1
+    ref = np.array([oracle.bhattacharyya_lnz(n, i, lnz0) for i in range(N)])
+    assert np.allclose(lnz, ref, rtol=1e-12, atol=1e-300)
+    K = N // 2
+    frozen, _ = api.polar_construct(N, K, design_db, rate)
+    order = sorted(range(N), key=lambda i: (lnz[i], -i))
+    assert set(order[:K]) == set(np.nonzero(frozen == 0)[0].tolist())
+
+
+def test_decided_mask_and_its_validation(lib):
+    code = api.make_code(256, 128, 16)
+    m = api.decided_mask(code, 40)
+    assert m.sum() == 40 and not (m & code.frozen).any()
+    da = api.PolarCode(256, 128, 16, code.frozen, decided=m)
+    assert lib.polar_workspace_bytes(da.ref(), 10, 8, 2) > 0
+    bad = m.copy()
+    bad[np.nonzero(code.frozen)[0][0]] = 1
+    wrong = api.PolarCode(256, 128, 16, code.frozen, decided=bad)
+    assert lib.polar_workspace_bytes(wrong.ref(), 10, 8, 2) == 0
+    rc = lib.scl_decode(wrong.ref(), None, 4, 8, None, None, None, 0, None)
+    assert rc == -1 and "scl_decided" in lib.polar_last_error().decode()

@@ -136,6 +136,32 @@ def test_hybrid_prepared_weights_reused(precision):
         dec.hybrid(dev(llr), 12, M, other, pw)
 
 
+@pytest.mark.parametrize("N,K,crc,L,frac", [(256, 128, 16, 4, 0.5), (1024, 512, 16, 8, 0.25), (1024, 512, 16, 16, 0.5),
+                                         (2048, 1024, 24, 32, 0.3), (128, 64, 8, 2, 0.9)])
+def test_decision_aided_scl_and_hybrid_bit_exact(N, K, crc, L, frac):
+    """Decision-aided CA-SCL (the most reliable information positions decided without branching):
+    scl_decode and the hybrid decoder against the oracle with the same mask."""
+    import dataclasses
+    ocode0 = fr.oracle_code(N, K, crc)
+    code0 = fr.api_code(ocode0)
+    mask = api.decided_mask(code0, int(frac * K))
+    ocode = dataclasses.replace(ocode0, decided=mask)
+    code = api.PolarCode(N, K, crc, ocode0.frozen.copy(), ocode0.crc_poly, decided=mask)
+    _, llr = fr.frames(ocode, 1.0, 45, seed=7070 + N + L)
+    ref = oracle.scl_decode(llr, ocode, L, "f32")
+    dec = api.Decoder(code, 45, L)
+    bits, status = dec.scl(dev(llr))
+    torch.cuda.synchronize()
+    assert np.array_equal(status.cpu().numpy(), ref["status"])
+    assert np.array_equal(api.unpack_bits(bits.cpu().numpy(), ocode.P), oracle.payload_of(ref["u_hat"], ocode))
+    href = oracle.hybrid_decode(llr, ocode, 30, 20.0, L, precision="f32")
+    bits, status, iters = dec.hybrid(dev(llr), 30, 20.0)
+    torch.cuda.synchronize()
+    assert np.array_equal(status.cpu().numpy(), href["status"])
+    assert np.array_equal(iters.cpu().numpy().astype(np.int32), href["iters"])
+    assert np.array_equal(api.unpack_bits(bits.cpu().numpy(), ocode.P), oracle.payload_of(href["u_hat"], ocode))
+
+
 def test_bp_edge_inputs():
     """NaN reads as an erasure, +-inf clips, max_iters = 1, a single frame."""
     ocode = fr.oracle_code(256, 128, 16)
