@@ -98,7 +98,28 @@ def _declare(L):
             _f32p, _c_int, _c_int, _u8p, _u8p, _i32p, _c_int, _c_uint, _c_int, _c_int, _u8p, _u8p, _f64p]
         getattr(L, "or_hybrid_decode_batch_" + sfx).argtypes = [
             _f32p, _c_int, _c_int, _u8p, _u8p, _i32p, _c_int, _c_uint, _c_int, _c_int, _c_double, _c_int,
-            _f32p, _c_int, _u8p, _u8p, _i32p]
+            _c_int, _f32p, _c_int, _u8p, _u8p, _i32p]
+    for sfx in ("f32", "f64", "f16"):
+        getattr(L, "or_pe_g_exact_" + sfx).argtypes = [_c_double, _c_double]
+        getattr(L, "or_pe_g_exact_" + sfx).restype = _c_double
+
+
+# BP mode bits of the C library (or_bp_decode): stopping rule and PE function (Sec. II-B)
+BP_CRC_STOP, BP_REENC_STOP, BP_G_EXACT = 1, 2, 4
+
+
+def bp_mode(early_stop: bool = True, stop: str = "crc", g: str = "minsum") -> int:
+    """Mode bits: stop "crc" (the CRC of u, the paper's rule) or "reencode" (HD(LLR(x)) equals the
+    re-encoded HD(LLR(u))); g "minsum" or "exact"."""
+    if stop not in ("crc", "reencode") or g not in ("minsum", "exact"):
+        raise ValueError("stop in {crc, reencode}, g in {minsum, exact}")
+    m = (BP_CRC_STOP if stop == "crc" else BP_REENC_STOP) if early_stop else 0
+    return m | (BP_G_EXACT if g == "exact" else 0)
+
+
+def pe_g_exact(a: float, b: float, precision: str = "f64") -> float:
+    """The exact PE function g(a, b) of Sec. II-B as the BP of the given precision evaluates it."""
+    return float(getattr(lib(), "or_pe_g_exact_" + precision)(a, b))
 
 
 def _dec(code):
@@ -250,8 +271,10 @@ def round_half(x: float) -> float:
 
 # ---------------------------------------------------------------- decoders
 def bp_decode(llr, code: Code, max_iters: int, llr_max: float, precision: str = "f32",
-              early_stop: bool = True, w=None, want_llr: bool = True, llr_u_double: bool = False) -> dict:
-    """Min-sum BP with CRC early stop on a batch llr float32 [B][N] (Sec. II-B)."""
+              early_stop: bool = True, w=None, want_llr: bool = True, llr_u_double: bool = False,
+              stop: str = "crc", g: str = "minsum") -> dict:
+    """BP with early stop on a batch llr float32 [B][N] (Sec. II-B): min-sum or exact g, CRC or
+    re-encoding stop (bp_mode)."""
     llr = _f32(llr).reshape(-1, code.N)
     B, N = llr.shape
     u = np.zeros((B, N), np.uint8)
@@ -267,7 +290,7 @@ def bp_decode(llr, code: Code, max_iters: int, llr_max: float, precision: str = 
         assert w.shape == (w_iters, 2, code.n, N)  # iterations past w_iters run unweighted
     getattr(lib(), "or_bp_decode_batch_" + precision)(
         _p(llr, _f32p), B, N, _p(code.frozen, _u8p), _p(code.info_idx, _i32p), code.K,
-        code.crc_poly, code.crc_len, max_iters, llr_max, int(early_stop), _p(w, _f32p), w_iters,
+        code.crc_poly, code.crc_len, max_iters, llr_max, bp_mode(early_stop, stop, g), _p(w, _f32p), w_iters,
         _p(u, _u8p), _p(st, _u8p), _p(it, _i32p), _p(lu, _f32p), _p(lx, _f32p), _p(lud, _f64p))
     return {"u_hat": u, "status": st, "iters": it, "llr_u": lu, "llr_x": lx, "llr_u_f64": lud}
 
@@ -339,8 +362,9 @@ def scl_list(llr_row, code: Code, L: int, precision: str = "f32"):
 
 
 def hybrid_decode(llr, code: Code, max_iters: int, llr_max: float, L: int, w=None,
-                  precision: str = "f32") -> dict:
-    """Sec. III hybrid: BP with CRC stop, CA-SCL on the frames BP leaves failed."""
+                  precision: str = "f32", stop: str = "crc", g: str = "minsum") -> dict:
+    """Sec. III hybrid: BP with CRC stop (or the re-encoding stop), CA-SCL on the frames whose CRC
+    fails when BP stops."""
     llr = _f32(llr).reshape(-1, code.N)
     B, N = llr.shape
     u = np.zeros((B, N), np.uint8)
@@ -352,7 +376,8 @@ def hybrid_decode(llr, code: Code, max_iters: int, llr_max: float, L: int, w=Non
         w_iters = w.shape[0]
     getattr(lib(), "or_hybrid_decode_batch_" + precision)(
         _p(llr, _f32p), B, N, _p(code.frozen, _u8p), _p(_dec(code), _u8p), _p(code.info_idx, _i32p), code.K,
-        code.crc_poly, code.crc_len, max_iters, llr_max, L, _p(w, _f32p), w_iters, _p(u, _u8p),
+        code.crc_poly, code.crc_len, max_iters, llr_max, bp_mode(True, stop, g), L, _p(w, _f32p), w_iters,
+        _p(u, _u8p),
         _p(st, _u8p), _p(it, _i32p))
     return {"u_hat": u, "status": st, "iters": it}
 

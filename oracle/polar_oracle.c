@@ -222,6 +222,16 @@ float or_round_half(float x)
     return (float)copysign(ldexp(r, q), (double)x);
 }
 
+/* BP modes (or_bp_decode's `mode`, or_hybrid_decode_batch's `bp_mode`), bits:                 */
+/*   OR_BP_CRC_STOP   stop when the CRC of the hard-decided u holds (Sec. II-B, the paper's rule) */
+/*   OR_BP_REENC_STOP stop when the hard decision of LLR(x) equals the re-encoded hard decision  */
+/*                    of LLR(u), x = u G (Sec. II-B, the stopping condition the CRC replaces)     */
+/*   OR_BP_G_EXACT    the exact PE function g(a, b) = ln((1 + e^(a+b)) / (e^a + e^b)) instead of  */
+/*                    the min-sum approximation (Sec. II-B)                                       */
+#define OR_BP_CRC_STOP 1
+#define OR_BP_REENC_STOP 2
+#define OR_BP_G_EXACT 4
+
 /* ------------------------------------------------------------------------------------------ */
 /* Type-generic decoders: BP, SC, SCL, hybrid, in FP32 (bit-exact parity target), FP64 (judge)  */
 /* and FP16-emulated (half-precision BP messages).                                           */

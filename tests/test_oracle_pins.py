@@ -486,3 +486,126 @@ def test_decision_aided_empty_mask_is_plain_and_noiseless_decodes():
     out = oracle.scl_decode(20.0 * (1.0 - 2.0 * x.astype(np.float32)), code, 4)
     assert np.array_equal(oracle.payload_of(out["u_hat"], code), pay)
     assert (out["status"] == 2).all()
+
+
+# ----------------------------------------------------- exact PE function and re-encoding stop
+def _kron_G(N):
+    F = np.array([[1, 0], [1, 1]], dtype=np.int64)
+    G = np.array([[1]], dtype=np.int64)
+    while G.shape[0] < N:
+        G = np.kron(G, F)
+    return G
+
+
+def _tanh_rule(lams):
+    """Posterior LLR of the XOR of independent bits with LLRs lams (the textbook tanh rule)."""
+    return float(2.0 * np.arctanh(np.prod(np.tanh(np.asarray(lams, np.float64) / 2.0))))
+
+
+def test_exact_g_is_the_tanh_rule():
+    """g(a, b) = ln((1 + e^(a+b)) / (e^a + e^b)) is the LLR of the XOR of two independent bits:
+    2 atanh(tanh(a/2) tanh(b/2)); symmetric, odd in each argument, |g| <= min(|a|, |b|) and the
+    min-sum approximation overshoots by at most ln 2."""
+    rng = np.random.default_rng(12)
+    for _ in range(400):
+        a, b = (float(v) for v in rng.uniform(-15, 15, 2))
+        g = oracle.pe_g_exact(a, b)
+        assert g == pytest.approx(_tanh_rule([a, b]), abs=1e-9)
+        assert g == oracle.pe_g_exact(b, a)
+        assert oracle.pe_g_exact(-a, b) == pytest.approx(-g, abs=1e-12)
+        m = min(abs(a), abs(b))
+        assert abs(g) <= m and m - abs(g) <= math.log(2.0) + 1e-12
+        assert np.sign(g) == np.sign(a) * np.sign(b)
+    assert oracle.pe_g_exact(3.0, 0.0) == 0.0
+    assert oracle.pe_g_exact(-3.0, 40.0) == pytest.approx(-3.0, abs=1e-12)
+
+
+@pytest.mark.parametrize("N", [8, 16, 64])
+def test_bp_first_l_sweep_is_the_exact_posterior_of_u(N):
+    """No frozen bit: u = x G with the x_i independent given y, so the posterior LLR of u_j is the
+    tanh rule over {i : G[i][j] = 1}.  Every R message stays 0 in the first iteration, and its L
+    sweep computes exactly that with the exact g, and sign product times smallest magnitude with
+    the min-sum g (G from np.kron, independent of the oracle)."""
+    G = _kron_G(N)
+    code = _code_from(N, range(N))
+    rng = np.random.default_rng(N)
+    lam = np.clip(rng.normal(1.5, 2.0, (5, N)), -8, 8).astype(np.float32)
+    ex = oracle.bp_decode(lam, code, 1, 20.0, "f64", early_stop=False, g="exact")
+    ms = oracle.bp_decode(lam, code, 1, 20.0, "f64", early_stop=False)
+    for b in range(5):
+        for j in range(N):
+            S = np.nonzero(G[:, j])[0]
+            v = lam[b, S].astype(np.float64)
+            assert ex["llr_u"][b, j] == pytest.approx(_tanh_rule(v), rel=1e-6, abs=1e-6), (b, j)
+            assert ms["llr_u"][b, j] == np.float32(np.prod(np.sign(v)) * np.min(np.abs(v))), (b, j)
+
+
+@pytest.mark.parametrize("N", [8, 32])
+def test_bp_first_r_sweep_is_the_prior_of_x(N):
+    """Zero channel LLRs: the first R sweep sees no channel information, so R[n+1] -- and LLR(x)
+    after one iteration -- is the prior of x = u G from the u-side LLRs alone: the tanh rule over
+    {j : G[j][i] = 1} of LLR_max (frozen u_j = 0) and 0 (free u_j)."""
+    G = _kron_G(N)
+    rng = np.random.default_rng(N + 1)
+    for _ in range(4):
+        info = sorted(rng.choice(N, size=N // 4, replace=False).tolist())
+        code = _code_from(N, info)
+        out = oracle.bp_decode(np.zeros((1, N), np.float32), code, 1, 20.0, "f64", early_stop=False, g="exact")
+        for i in range(N):
+            T = np.nonzero(G[:, i])[0]
+            prior = [20.0 if code.frozen[j] else 0.0 for j in T]
+            assert out["llr_x"][0, i] == pytest.approx(_tanh_rule(prior), abs=4e-6), (info, i)
+
+
+@pytest.mark.parametrize("g", ["minsum", "exact"])
+def test_reencoding_stop_rule(g):
+    """The re-encoding stop ends BP at the first iteration t where HD(LLR(x)) = HD(LLR(u)) G (G from
+    np.kron), checked on the outputs of runs of t and t - 1 iterations without early stop; the
+    frame counts as decoded iff the CRC of that u holds."""
+    code = oracle.make_code(64, 32, 8)
+    G = _kron_G(64)
+    _, _, llr = _noisy_frames(code, 2.0, 24, 31)
+    imax = 25
+    r = oracle.bp_decode(llr, code, imax, 20.0, "f32", stop="reencode", g=g)
+
+    def holds(b, T):
+        o = oracle.bp_decode(llr[b:b + 1], code, T, 20.0, "f32", early_stop=False, g=g)
+        x = (o["u_hat"][0].astype(np.int64) @ G) % 2
+        return np.array_equal(x, (o["llr_x"][0] < 0).astype(np.int64)), o
+
+    stopped_early = 0
+    for b in range(llr.shape[0]):
+        t = int(r["iters"][b])
+        ok, o = holds(b, t)
+        assert ok or t == imax, b
+        stopped_early += t < imax
+        if t > 1:
+            assert not holds(b, t - 1)[0], b
+        assert np.array_equal(o["u_hat"][0], r["u_hat"][b])
+        crc_ok = oracle.crc_check(o["u_hat"][0][code.info_idx], code.crc_poly, code.crc_len)
+        assert (r["status"][b] == oracle.BP_OK) == crc_ok, b
+    assert stopped_early >= 12
+
+
+def test_exact_g_and_reencoding_noiseless_and_hybrid():
+    """Noiseless frames decode exactly with every stop rule and g; the hybrid with either stop rule
+    is BP followed by CA-SCL on exactly the frames whose CRC fails when BP stops."""
+    code = oracle.make_code(128, 64, 8)
+    pay = inputs.payload_bits(3, 0, 8, code.P)
+    x = oracle.encode_batch(pay, code)
+    llr = (8.0 * (1.0 - 2.0 * x)).astype(np.float32)
+    u_true = np.stack([oracle.build_u(p, code) for p in pay])
+    for stop in ("crc", "reencode"):
+        for g in ("minsum", "exact"):
+            bp = oracle.bp_decode(llr, code, 50, 20.0, stop=stop, g=g)
+            assert np.array_equal(bp["u_hat"], u_true) and np.all(bp["status"] == oracle.BP_OK), (stop, g)
+    _, _, noisy = _noisy_frames(code, 1.5, 60, 17)
+    for stop in ("crc", "reencode"):
+        bp = oracle.bp_decode(noisy, code, 10, 20.0, stop=stop, g="exact")
+        hy = oracle.hybrid_decode(noisy, code, 10, 20.0, 4, stop=stop, g="exact")
+        scl = oracle.scl_decode(noisy, code, 4)
+        ok = bp["status"] == oracle.BP_OK
+        assert 0 < ok.sum() < len(ok)
+        assert np.array_equal(hy["iters"], bp["iters"])
+        assert np.array_equal(hy["u_hat"][ok], bp["u_hat"][ok])
+        assert np.array_equal(hy["u_hat"][~ok], scl["u_hat"][~ok])
