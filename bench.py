@@ -19,6 +19,10 @@ Other workloads (`--workload`, one JSON line each, same keys):
   stress  N = 2048, K = 1024 (CRC-24 0x864CFB), 1.5 dB, 1e6 frames per step in batches of 2^16:
           learned FP16 BP (20 iterations; plain FP16 if no trained weights for this code) then
           CA-SCL L = 32; reports the CA-SCL share of the runtime and the batch latency p50/p99.
+  paper   the paper's own configuration: N = 4096, K = 2048 (incl. CRC-16), BP with the exact PE
+          function in FP32 (clip 20), i_max = 50, CA-SCL L = 32, swept over Eb/N0 (FER, BER,
+          fallback rate, throughput and batch latency per point, min-sum FP32 and half2 beside);
+          `value` is the largest exact-g throughput of the sweep, the quantity the paper reports.
 """
 from __future__ import annotations
 
@@ -45,7 +49,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["hybrid", "mixed", "stress"], default="hybrid")
+    ap.add_argument("--workload", choices=["hybrid", "mixed", "stress", "paper"], default="hybrid")
+    ap.add_argument("--paper-frames", type=int, default=32768, help="frames per step of --workload paper")
+    ap.add_argument("--paper-ebn0", type=float, nargs="+", default=[1.0, 1.5, 2.0, 2.5, 3.0, 4.0, 5.0])
     ap.add_argument("--precision", choices=["fp32", "fp16"], default="fp32")
     ap.add_argument("--ebn0", type=float, default=2.5)
     ap.add_argument("--frames", type=int, default=100_000)
@@ -53,6 +59,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the host-scheduled, re-encoding-stop and exact-g blocks of the default line")
     ap.add_argument("--da-bits", type=int, default=128,
                     help="decision-aided block: information positions CA-SCL decides without branching")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1609_09358_gb300", "weights", "wms_n1024_k512_t20.pt"))
@@ -213,6 +221,8 @@ def main():
         return run_mixed(a, world, rank, local)
     if a.workload == "stress":
         return run_stress(a, world, rank, local)
+    if a.workload == "paper":
+        return run_paper(a, world, rank, local)
 
     import numpy as np
     import torch
@@ -324,10 +334,22 @@ def main():
             "bp_ms_per_step": bp_ms / a.steps, "scl_ms_per_step": scl_ms / a.steps,
             "gpu_launches": bp_n + scl_n, "roofline": roofline, "clocks": clocks}
 
+    # Eq. (1): hybrid throughput predicted from the BP and CA-SCL kernels' own throughputs and the
+    # BP frame-error (fallback) rate, without launch overhead; against the measured value
+    t_bp = P * B / (bp_ms / a.steps * 1e-3) / 1e9
+    t_scl = P * n_fb / (scl_ms / a.steps * 1e-3) / 1e9 if scl_ms > 0 else None
+    gamma = n_fb / B
+    theo = t_bp * t_scl / (t_scl + gamma * t_bp) if t_scl else t_bp
+    line["eq1"] = {"t_bp_gbit_s": t_bp, "t_scl_gbit_s": t_scl, "gamma_bp_fer": gamma, "theo_gbit_s": theo,
+                   "measured_over_theo": value / world / theo}
     if prec == api.POLAR_FP32 and not a.no_learned:
         line["plain_fp16"] = plain_fp16(a, code, llr, payload, stream, dist)
         if a.da_bits > 0:
             line["decision_aided"] = decision_aided(a, code, llr, payload, stream, dist)
+        if not a.no_variants:
+            line["host_scheduled"] = host_scheduled(a, code, llr, payload, stream, dist)
+            line["reencode_stop"] = bp_variant(a, code, llr, payload, stream, dist, api.POLAR_STOP_REENCODE, 50)
+            line["exact_g"] = bp_variant(a, code, llr, payload, stream, dist, api.POLAR_G_EXACT, 5)
     if not a.no_learned and os.path.exists(a.weights):
         line["learned_fp16"] = learned(a, llr, payload, stream, dist)
         line["learned_fp16_imax%d" % IMAX] = learned(a, llr, payload, stream, dist, IMAX)
@@ -345,25 +367,16 @@ def main():
     return 0
 
 
-def decision_aided(a, code, llr, payload, stream, dist):
-    """Decision-aided CA-SCL (Sec. II-A) on the same frames: the da_bits most reliable information
-    positions (Bhattacharyya at the construction's design point) are decided by each path's hard
-    decision without branching the list; FP32 BP as in the main line."""
+def _timed_variant(a, code, dec, step, payload, stream, dist, max_steps=50):
+    """Time `step` (one decode of the batch with decoder `dec`) over min(steps, max_steps) steps on
+    the same frames after warm-up; decoding statistics of the last step."""
     import torch
 
     from paper_1609_09358_gb300 import api
-    mask = api.decided_mask(code, a.da_bits)
-    dcode = api.PolarCode(code.N, code.K, code.crc_len, code.frozen, code.crc_poly, decided=mask)
-    B = llr.shape[0]
-    dec = api.Decoder(dcode, B, LIST, device=llr.device)
-
-    def step():
-        dec.hybrid(llr, IMAX, LLR_MAX, api.POLAR_FP32)
-
     for _ in range(max(a.warmup, 1)):
         step()
     torch.cuda.synchronize()
-    steps = max(1, min(a.steps, 50))
+    steps = max(1, min(a.steps, max_steps))
     if dist:
         dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -374,55 +387,61 @@ def decision_aided(a, code, llr, payload, stream, dist):
     e1.record(stream)
     torch.cuda.synchronize()
     api.polar_profile_enable(False)
-    bp_ms, _, scl_ms, _ = api.polar_profile_read()
-    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=llr.device)
+    bp_ms, bp_n, scl_ms, scl_n = api.polar_profile_read()
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=payload.device)
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     world = dist.get_world_size() if dist else 1
+    B = payload.shape[0]
     ferr = (dec.bits != payload).any(dim=1)
     return {"value": world * code.P * B * steps / (float(t.item()) * 1e-3) / 1e9, "unit": "Gbit/s", "steps": steps,
             "ms_per_step": float(t.item()) / steps, "fer": float(ferr.float().mean().item()),
             "fallback_rate": float((dec.status != api.FRAME_BP_OK).float().mean().item()),
-            "da_bits": a.da_bits, "bp_ms_per_step": bp_ms / steps, "scl_ms_per_step": scl_ms / steps, "dtype": "f32"}
+            "avg_bp_iters": float(dec.iters.float().mean().item()),
+            "bp_ms_per_step": bp_ms / steps, "scl_ms_per_step": scl_ms / steps,
+            "launches_per_step": (bp_n + scl_n) / steps}
+
+
+def decision_aided(a, code, llr, payload, stream, dist):
+    """Decision-aided CA-SCL (Sec. II-A) on the same frames: the da_bits most reliable information
+    positions (Bhattacharyya at the construction's design point) are decided by each path's hard
+    decision without branching the list; FP32 BP as in the main line."""
+    from paper_1609_09358_gb300 import api
+    mask = api.decided_mask(code, a.da_bits)
+    dcode = api.PolarCode(code.N, code.K, code.crc_len, code.frozen, code.crc_poly, decided=mask)
+    dec = api.Decoder(dcode, llr.shape[0], LIST, device=llr.device)
+    r = _timed_variant(a, code, dec, lambda: dec.hybrid(llr, IMAX, LLR_MAX, api.POLAR_FP32), payload, stream, dist)
+    return {**r, "da_bits": a.da_bits, "dtype": "f32"}
+
+
+def bp_variant(a, code, llr, payload, stream, dist, flags, max_steps):
+    """A BP variant of Sec. II-B in the FP32 hybrid on the same frames: the exact PE function
+    (POLAR_G_EXACT) and/or the re-encoding stop (POLAR_STOP_REENCODE); CA-SCL as in the main line."""
+    from paper_1609_09358_gb300 import api
+    dec = api.Decoder(code, llr.shape[0], LIST, device=llr.device)
+    r = _timed_variant(a, code, dec, lambda: dec.hybrid(llr, IMAX, LLR_MAX, api.POLAR_FP32 | flags), payload,
+                       stream, dist, max_steps)
+    return {**r, "i_max": IMAX, "dtype": "f32"}
+
+
+def host_scheduled(a, code, llr, payload, stream, dist):
+    """The host-scheduled hybrid of Fig. 3 on the same frames (hybrid_decode_scheduled: chunks of
+    16384 frames in BP on three streams, polled by the host, CA-SCL started on each finished chunk's
+    failures when the CA-SCL stream is idle), against the main line's two stream-ordered launches."""
+    from paper_1609_09358_gb300 import api
+    dec = api.Decoder(code, llr.shape[0], LIST, device=llr.device)
+    r = _timed_variant(a, code, dec, lambda: dec.scheduled(llr, IMAX, LLR_MAX, api.POLAR_FP32, chunk=16384),
+                       payload, stream, dist)
+    return {**r, "chunk": 16384, "bp_streams": api.POLAR_SCHED_BP_STREAMS, "dtype": "f32"}
 
 
 def plain_fp16(a, code, llr, payload, stream, dist):
     """The plain half2 form on the same frames: binary16 BP messages (clip 32), i_max = 200, then
     CA-SCL L = 8 in FP32 on the CRC failures."""
-    import torch
-
     from paper_1609_09358_gb300 import api
-    B = llr.shape[0]
-    dec = api.Decoder(code, B, LIST, device=llr.device)
-
-    def step():
-        dec.hybrid(llr, IMAX, 32.0, api.POLAR_FP16)
-
-    for _ in range(max(a.warmup, 1)):
-        step()
-    torch.cuda.synchronize()
-    steps = max(1, min(a.steps, 50))
-    if dist:
-        dist.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    api.polar_profile_enable(True)
-    e0.record(stream)
-    for _ in range(steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    api.polar_profile_enable(False)
-    bp_ms, _, scl_ms, _ = api.polar_profile_read()
-    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=llr.device)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    world = dist.get_world_size() if dist else 1
-    ferr = (dec.bits != payload).any(dim=1)
-    return {"value": world * code.P * B * steps / (float(t.item()) * 1e-3) / 1e9, "unit": "Gbit/s", "steps": steps,
-            "ms_per_step": float(t.item()) / steps, "fer": float(ferr.float().mean().item()),
-            "fallback_rate": float((dec.status != api.FRAME_BP_OK).float().mean().item()),
-            "avg_bp_iters": float(dec.iters.float().mean().item()), "i_max": IMAX,
-            "bp_ms_per_step": bp_ms / steps, "scl_ms_per_step": scl_ms / steps, "dtype": "f16"}
+    dec = api.Decoder(code, llr.shape[0], LIST, device=llr.device)
+    r = _timed_variant(a, code, dec, lambda: dec.hybrid(llr, IMAX, 32.0, api.POLAR_FP16), payload, stream, dist)
+    return {**r, "i_max": IMAX, "dtype": "f16"}
 
 
 def learned(a, llr, payload, stream, dist, imax=None):
@@ -750,6 +769,135 @@ def run_stress(a, world, rank, local):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+# ----------------------------------------------------------------------------- the paper's workload
+PA_N, PA_K, PA_CRC, PA_L, PA_IMAX = 4096, 2048, 16, 32, 50
+PAPER_GBIT_S = 0.034  # the paper's largest hybrid throughput on this workload (GTX 980 Ti + i7-4790K)
+
+
+def run_paper(a, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1609_09358_gb300 import api, build
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    api.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    code = api.make_code(PA_N, PA_K, PA_CRC, 0.0)
+    B, P, N = a.paper_frames, code.P, code.N
+    frame0 = rank * B
+    payload = torch.empty((B, code.row_bytes), dtype=torch.uint8, device=dev)
+    cw = torch.empty((B, N // 8), dtype=torch.uint8, device=dev)
+    llr = torch.empty((B, N), dtype=torch.float32, device=dev)
+    dec = api.Decoder(code, B, PA_L, device=dev)
+    api.polar_random_payload(B, P, SEED + 11, frame0, payload)
+    api.polar_encode(code, payload, cw)
+    variants = [("exact_g", api.POLAR_FP32 | api.POLAR_G_EXACT, LLR_MAX), ("min_sum", api.POLAR_FP32, LLR_MAX),
+                ("min_sum_fp16", api.POLAR_FP16, 32.0)]
+    steps = max(1, min(a.steps, 5))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max_mhz = float(_peaks().get("sm_max_mhz", 2070.0))
+    points, launches = [], 0
+    for e in a.paper_ebn0:
+        sigma = float(np.sqrt(1.0 / (2.0 * (P / N) * 10 ** (e / 10.0))))
+        api.polar_awgn_llr(cw, N, sigma, SEED + 11, frame0, llr)
+        pt = {"ebn0_db": e}
+        for name, prec, M in variants:
+            def step():
+                dec.hybrid(llr, PA_IMAX, M, prec)
+            for _ in range(max(a.warmup, 1)):
+                step()
+            torch.cuda.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            it_ev = iter(evs)
+
+            def timed_step():
+                e0, e1 = next(it_ev)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+
+            api.polar_profile_enable(True)
+            ms, clocks = _timed(timed_step, steps, stream, local, dist)
+            api.polar_profile_enable(False)
+            bp_ms, bp_n, scl_ms, scl_n = api.polar_profile_read()
+            launches += bp_n + scl_n
+            lat = [e0.elapsed_time(e1) for e0, e1 in evs]
+            ferr, nbit = _popcount_errors(dec.bits, payload)
+            it = dec.iters.cpu().numpy().astype(np.int64)
+            r = {"gbit_s": world * P * B * steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / steps,
+                 "fer": float(ferr.float().mean().item()), "ber": nbit / (B * P),
+                 "fallback_rate": float((dec.status != api.FRAME_BP_OK).float().mean().item()),
+                 "avg_bp_iters": float(it.mean()), "bp_ms_per_step": bp_ms / steps, "scl_ms_per_step": scl_ms / steps,
+                 "batch_latency_ms": {"mean": float(np.mean(lat)), "max": float(np.max(lat))}, "clocks": clocks}
+            if name == "exact_g":
+                # the exact PE function is bound by the special-function units: 4 of their operations
+                # (2 exponentials, 2 logarithms) per g, 2 n N g per frame-iteration, against
+                # SMs x 16 per clock (compute capability 10.x) x clock
+                ops = 4.0 * 2 * code.n * N * float(it.sum()) * steps
+                peak = sms * 16 * sm_max_mhz * 1e6
+                ach = ops / (bp_ms * 1e-3) if bp_ms > 0 else 0.0
+                r["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "Top/s",
+                                 "frac": ach / peak, "traffic": None, "kernel": "bp_kernel (exact g)",
+                                 "peak_basis": "%d SMs x 16 special-function results per clock x %.0f MHz"
+                                               % (sms, sm_max_mhz)}
+            else:
+                ops = float((6 * code.n * N + code.K) * it.sum()) * steps
+                r["roofline"] = _alu_roofline(ops, bp_ms, prec == api.POLAR_FP16, dev)
+            pt[name] = r
+        points.append(pt)
+    best = max(points, key=lambda p: p["exact_g"]["gbit_s"])
+    value = best["exact_g"]["gbit_s"]
+    line = {"metric": "info Gbit/s, N=4096 R=1/2 hybrid BP (exact g, FP32, i_max=50) + CA-SCL L=32, the largest "
+                      "over the Eb/N0 sweep", "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": steps,
+            "warmup": a.warmup, "ms_per_step": best["exact_g"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": value / PAPER_GBIT_S, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "the paper's configuration: N=%d K=%d (incl. CRC-16 0x1021), BPSK-AWGN, exact-g FP32 "
+                                   "BP i_max=%d with CRC stop, CA-SCL L=%d; %d frames per step per GPU; Eb/N0 sweep %s dB"
+                                   % (PA_N, PA_K, PA_IMAX, PA_L, B, a.paper_ebn0),
+                       "best_ebn0_db": best["ebn0_db"],
+                       "cache": "inputs larger than L2 (%.0f MB of LLRs per step), no flush" % (B * N * 4 / 1e6),
+                       "baseline": "34 Mbit/s: the paper's maximum on a GTX 980 Ti (context, other hardware)"},
+            "fer": best["exact_g"]["fer"], "ber": best["exact_g"]["ber"],
+            "fallback_rate": best["exact_g"]["fallback_rate"], "avg_bp_iters": best["exact_g"]["avg_bp_iters"],
+            "sweep": points, "gpu_launches": launches, "roofline": best["exact_g"]["roofline"],
+            "clocks": best["exact_g"]["clocks"]}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = _paper_oracle_rate(best["ebn0_db"])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _paper_oracle_rate(ebn0: float, min_seconds: float = 10.0):
+    """The oracle (exact g, FP64 BP then CA-SCL) on seeded frames of the paper's workload."""
+    import numpy as np
+
+    import oracle
+    from paper_1609_09358_gb300 import inputs
+    ocode = oracle.make_code(PA_N, PA_K, PA_CRC, 0.0)
+    sigma = oracle.sigma_for(ebn0, ocode.P / PA_N)
+    done, secs, frame0, nb = 0, 0.0, 0, 4 * max(1, oracle.num_threads())
+    while secs < min_seconds:
+        pay = inputs.payload_bits(SEED + 12, frame0, nb, ocode.P)
+        x = oracle.encode_batch(pay, ocode)
+        llr = oracle.channel_llr(x, inputs.unit_noise(SEED + 12, frame0, nb, PA_N), sigma)
+        t0 = time.perf_counter()
+        oracle.hybrid_decode(llr, ocode, PA_IMAX, LLR_MAX, PA_L, precision="f64", g="exact")
+        secs += time.perf_counter() - t0
+        done += nb
+        frame0 += nb
+    return {"value": ocode.P * done / secs / 1e9, "unit": "Gbit/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d seeded frames at %.1f dB (%.1f s), C oracle, exact g in FP64, OpenMP" % (done, ebn0, secs)}
 
 
 if __name__ == "__main__":

@@ -52,14 +52,27 @@ extern "C" {
 /* bp_decode only, OR-ed into precision: run exactly max_iters iterations (no CRC early stop);
  * the status still reports whether the CRC of the final hard decision holds. */
 #define POLAR_FIXED_ITERS 0x100
+/* BP variants of Sec. II-B, OR-ed into `precision` of bp_decode / hybrid_decode /
+ * hybrid_decode_host / hybrid_decode_noalloc (POLAR_FP32 messages, no learned weights):
+ *   POLAR_G_EXACT        the exact PE function g(a, b) = ln((1 + e^(a+b)) / (e^a + e^b)) instead of
+ *                        min-sum; computed with fast exponentials and logarithms, so it matches an
+ *                        exact evaluation to about 1e-6 per update, not to the bit
+ *   POLAR_STOP_REENCODE  stop at the first iteration where HD(LLR(x)) equals the re-encoded
+ *                        HD(LLR(u)) (x = u G) instead of when the CRC holds; a frame counts as
+ *                        decoded (POLAR_FRAME_BP_OK, else CA-SCL in the hybrid) iff its CRC holds
+ *                        when BP stops */
+#define POLAR_G_EXACT 0x200
+#define POLAR_STOP_REENCODE 0x400
 
 #define POLAR_OP_BP 0
 #define POLAR_OP_SCL 1
 #define POLAR_OP_HYBRID 2
 #define POLAR_OP_HYBRID_HOST 3
+#define POLAR_OP_HYBRID_SCHED 4
 
 #define POLAR_MIN_N 128
-#define POLAR_MAX_N 2048
+#define POLAR_MAX_N 4096
+#define POLAR_MAX_N_MIXED 2048 /* mixed batches, learned weights and their training: N <= 2048 */
 #define POLAR_MAX_L 32
 #define POLAR_MAX_CODES 32
 
@@ -126,7 +139,9 @@ int polar_awgn_llr(const uint8_t* codeword, int32_t B, int32_t N, float sigma,
  * is CRC-checked and the frame stops when it passes.
  *   llr: device float [B][N].  max_iters >= 1.  llr_max > 0.
  *   precision: POLAR_FP32 (bit-exact with a binary32 reference) or POLAR_FP16 (binary16
- *     messages, llr_max <= 32768), optionally | POLAR_FIXED_ITERS.
+ *     messages, llr_max <= 32768), optionally | POLAR_FIXED_ITERS (run max_iters iterations
+ *     whatever the CRC), and for POLAR_FP32 without weights | POLAR_G_EXACT and/or
+ *     | POLAR_STOP_REENCODE (the variants of Sec. II-B described with those flags).
  *   wms_scales: NULL, or the learned weights of a weighted min-sum BP as prepared by
  *     wms_prepare for this code, wms_iters and precision (device, 16-byte aligned): each g term
  *     is multiplied by its scale before the clip; iterations t >= wms_iters run unweighted.
@@ -168,7 +183,7 @@ int hybrid_decode(const polar_code* code, const float* llr, int32_t B, int32_t m
  * The prepared buffer is then passed as wms_scales to bp_decode / hybrid_decode with the same
  * code, wms_iters and precision; preparing once and decoding many batches reads each scale with
  * one vector load per thread and stage.  wms_prepared_bytes returns 0 on invalid arguments.
- * Errors: POLAR_ERR_ARG (invalid code, N outside [128, 2048], wms_iters < 1, NULL or misaligned
+ * Errors: POLAR_ERR_ARG (invalid code, N outside [128, POLAR_MAX_N_MIXED], wms_iters < 1, NULL or misaligned
  * pointer), POLAR_ERR_WORKSPACE (buffer too small), POLAR_ERR_CUDA. */
 size_t wms_prepared_bytes(const polar_code* code, int32_t wms_iters, int32_t precision);
 int wms_prepare(const polar_code* code, const float* w, int32_t wms_iters, int32_t precision,
@@ -241,6 +256,26 @@ int hybrid_decode_host(const polar_code* code, const float* llr_host, int32_t B,
                        float llr_max, int32_t precision, const void* wms_scales, int32_t wms_iters,
                        int32_t L, uint8_t* bits_host, uint8_t* status_host, uint16_t* iters_host,
                        void* workspace, size_t ws_bytes, void* stream);
+
+/* Host-scheduled hybrid decoding: the scheduling of Fig. 3 (Sec. III), kept to measure what it
+ * costs against hybrid_decode's two stream-ordered launches.  The batch is cut into chunks of
+ * `chunk` frames.  While fewer than POLAR_SCHED_BP_STREAMS chunks are in BP, the host starts the
+ * next chunk's BP launch on a free library-owned stream ("enough buffer space"); it polls those
+ * launches, and when one has finished it reads that chunk's count of CRC failures ("BP finished");
+ * whenever failed frames are waiting and the CA-SCL stream is idle, it launches CA-SCL on them
+ * ("start idle SCL decoders": one launch per waiting chunk, on one library-owned stream).  Failed
+ * frames are not copied: BP lists their indices and CA-SCL reads their LLR rows in place.  The call
+ * returns once the last CA-SCL launch is issued (the host has seen every BP launch finish); work
+ * issued later on `stream` is ordered after all of it.  Results equal hybrid_decode's.
+ *   llr, bits, status, iters: device, as for hybrid_decode.  chunk: frames per BP launch, >= 256.
+ *   workspace: device, >= polar_workspace_bytes(code, B, L, POLAR_OP_HYBRID_SCHED) bytes.
+ *   Errors: as hybrid_decode; POLAR_ERR_ARG for chunk < 256; POLAR_ERR_TIMEOUT if a launch has
+ *   not finished 600 s after the host last saw progress. */
+#define POLAR_SCHED_BP_STREAMS 3
+int hybrid_decode_scheduled(const polar_code* code, const float* llr, int32_t B, int32_t max_iters,
+                            float llr_max, int32_t precision, const void* wms_scales, int32_t wms_iters,
+                            int32_t L, int32_t chunk, uint8_t* bits, uint8_t* status, uint16_t* iters,
+                            void* workspace, size_t ws_bytes, void* stream);
 
 /* Kernel timing for measurement (not a step of the paper).  While enabled on the calling host
  * thread, every decoder call brackets its BP and SCL kernel launches with CUDA events on the

@@ -18,7 +18,13 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpolar_gb300.so")
 POLAR_OK = 0
 POLAR_FP32, POLAR_FP16 = 0, 1
 POLAR_FIXED_ITERS = 0x100  # bp_decode: OR into precision to run exactly max_iters iterations
-POLAR_OP_BP, POLAR_OP_SCL, POLAR_OP_HYBRID, POLAR_OP_HYBRID_HOST = 0, 1, 2, 3
+# BP variants of Sec. II-B (OR into precision; FP32 messages, no learned weights): the exact PE
+# function instead of min-sum, and the re-encoding stop (HD(LLR(x)) = HD(LLR(u)) G) instead of the CRC
+POLAR_G_EXACT = 0x200
+POLAR_STOP_REENCODE = 0x400
+_MSG = 0xFF  # message-type part of precision
+POLAR_OP_BP, POLAR_OP_SCL, POLAR_OP_HYBRID, POLAR_OP_HYBRID_HOST, POLAR_OP_HYBRID_SCHED = 0, 1, 2, 3, 4
+POLAR_SCHED_BP_STREAMS = 3
 FRAME_BP_OK, FRAME_SCL_OK, FRAME_SCL_CRC_FAIL, FRAME_BP_FAIL = 1, 2, 3, 4
 CRC_POLYS = {0: 0x0, 8: 0x07, 16: 0x1021, 24: 0x864CFB}
 
@@ -60,6 +66,8 @@ SIGNATURES = {
                                           _sz, _vp]),
     "hybrid_decode_noalloc": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _i32, _vp, _i32, _i32, _vp, _vp, _vp,
                                              _vp]),
+    "hybrid_decode_scheduled": (ctypes.c_int, [_CP, _vp, _i32, _i32, _f32, _i32, _vp, _i32, _i32, _i32, _vp, _vp,
+                                               _vp, _vp, _sz, _vp]),
     "polar_mixed_workspace_bytes": (_sz, [_CP, _i32, _i32, _i32]),
     "hybrid_decode_mixed": (ctypes.c_int, [_CP, _i32, _vp, _vp, _vp, _i32, _i32, _f32, _i32, _i32, _vp, _i32, _vp, _vp,
                                            _vp, _sz, _vp]),
@@ -285,7 +293,7 @@ def bp_decode(code: PolarCode, llr, max_iters: int, llr_max: float, precision: i
               iters, llr_u=None, llr_x=None, workspace=None, stream=None) -> None:
     """wms_scales: None, PreparedScales, or CUDA float32 weights [T][2][n][N] (prepared per call)."""
     B = llr.shape[0]
-    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision & ~POLAR_FIXED_ITERS, stream)
+    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision & _MSG, stream)
     ws_b = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(load().bp_decode(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, wms_scales, w_iters,
                             _ptr(bits), _ptr(status), _ptr(iters), _ptr(llr_u), _ptr(llr_x), _ptr(workspace), ws_b,
@@ -302,7 +310,7 @@ def scl_decode(code: PolarCode, llr, L: int, bits, status, workspace, stream=Non
 def hybrid_decode(code: PolarCode, llr, max_iters: int, llr_max: float, precision: int, wms_scales, L: int, bits,
                   status, iters, workspace, stream=None) -> None:
     B = llr.shape[0]
-    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision, stream)
+    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision & _MSG, stream)
     ws_b = workspace.numel() * workspace.element_size()
     _check(load().hybrid_decode(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, wms_scales, w_iters,
                                 L, _ptr(bits), _ptr(status), _ptr(iters), _ptr(workspace), ws_b, _stream(stream)),
@@ -316,12 +324,26 @@ def hybrid_decode_host(code: PolarCode, llr_host, max_iters: int, llr_max: float
     for t in (llr_host, bits_host, status_host, iters_host):
         if t.is_cuda or not t.is_contiguous():
             raise PolarError("hybrid_decode_host expects contiguous host tensors")
-    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision, stream)
+    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision & _MSG, stream)
     ws_b = workspace.numel() * workspace.element_size()
     _check(load().hybrid_decode_host(code.ref(), llr_host.data_ptr(), B, max_iters, llr_max, precision,
                                      wms_scales, w_iters, L, bits_host.data_ptr(), status_host.data_ptr(),
                                      iters_host.data_ptr(), _ptr(workspace), ws_b, _stream(stream)),
            "hybrid_decode_host")
+
+
+def hybrid_decode_scheduled(code: PolarCode, llr, max_iters: int, llr_max: float, precision: int, wms_scales, L: int,
+                            chunk: int, bits, status, iters, workspace, stream=None) -> None:
+    """The host-scheduled hybrid of Fig. 3 (chunked BP launches polled by the host, CA-SCL started
+    on the chunks' failures when idle); device tensors as hybrid_decode, workspace of
+    POLAR_OP_HYBRID_SCHED size.  Blocks the calling thread until every BP launch has finished."""
+    B = llr.shape[0]
+    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision & _MSG, stream)
+    ws_b = workspace.numel() * workspace.element_size()
+    _check(load().hybrid_decode_scheduled(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, wms_scales,
+                                          w_iters, L, chunk, _ptr(bits), _ptr(status), _ptr(iters), _ptr(workspace),
+                                          ws_b, _stream(stream)),
+           "hybrid_decode_scheduled")
 
 
 def hybrid_decode_noalloc(code: PolarCode, llr, max_iters: int, llr_max: float, precision: int, wms_scales,
@@ -330,7 +352,7 @@ def hybrid_decode_noalloc(code: PolarCode, llr, max_iters: int, llr_max: float, 
     library's static scratch array is used instead (B <= 65536 frames, CA-SCL list in shared
     memory).  Calls that overlap on the GPU race on that array."""
     B = llr.shape[0]
-    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision, stream)
+    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision & _MSG, stream)
     _check(load().hybrid_decode_noalloc(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, wms_scales,
                                         w_iters, L, _ptr(bits), _ptr(status), _ptr(iters), _stream(stream)),
            "hybrid_decode_noalloc")
@@ -365,13 +387,19 @@ class Decoder:
         self.bits = torch.zeros((B, code.row_bytes), dtype=torch.uint8, device=device)
         self.status = torch.zeros(B, dtype=torch.uint8, device=device)
         self.iters = torch.zeros(B, dtype=torch.int16, device=device)
-        ws = max(polar_workspace_bytes(code, B, L, POLAR_OP_HYBRID), polar_workspace_bytes(code, B, L, POLAR_OP_SCL))
+        ws = max(polar_workspace_bytes(code, B, L, op) for op in (POLAR_OP_HYBRID, POLAR_OP_SCL, POLAR_OP_HYBRID_SCHED))
         self.workspace = torch.zeros(max(ws, 256), dtype=torch.uint8, device=device)
 
     def hybrid(self, llr, max_iters: int, llr_max: float = 20.0, precision: int = POLAR_FP32, wms_scales=None,
                stream=None):
         hybrid_decode(self.code, llr, max_iters, llr_max, precision, wms_scales, self.L, self.bits, self.status,
                       self.iters, self.workspace, stream)
+        return self.bits, self.status, self.iters
+
+    def scheduled(self, llr, max_iters: int, llr_max: float = 20.0, precision: int = POLAR_FP32, wms_scales=None,
+                  chunk: int = 16384, stream=None):
+        hybrid_decode_scheduled(self.code, llr, max_iters, llr_max, precision, wms_scales, self.L, chunk, self.bits,
+                                self.status, self.iters, self.workspace, stream)
         return self.bits, self.status, self.iters
 
     def bp(self, llr, max_iters: int, llr_max: float = 20.0, precision: int = POLAR_FP32, wms_scales=None,

@@ -100,35 +100,62 @@ struct BPPlan {
     static constexpr int XW = PAD ? ((N + (N >> 5) + (N >> 10)) + 3) & ~3 : N;
 };
 
+// Compile-time checks of a plan, one group at a time (each its own constant expression, so the
+// checks of long codes stay within the compiler's evaluation budget).
+template <class P, int G>
+constexpr bool plan_group_bijective()
+{
+    // group G maps (thread, register) onto the N nodes one to one
+    uint32_t seen[P::N / 32] = {};
+    for (int t = 0; t < P::T; ++t)
+        for (int k = 0; k < P::R; ++k) {
+            const int j = P::node(G, t, k);
+            if (j < 0 || j >= P::N || ((seen[j >> 5] >> (j & 31)) & 1u)) return false;
+            seen[j >> 5] |= 1u << (j & 31);
+        }
+    return true;
+}
+template <class P, int G, int K>
+constexpr bool plan_group_banks()
+{
+    // register K of the 32 threads of every warp: distinct banks; PAD plans: the address splits
+    // into the thread's base and the register's offset
+    for (int w = 0; w < P::NW; ++w) {
+        uint32_t banks = 0;
+        for (int l = 0; l < 32 && w * 32 + l < P::T; ++l) {
+            const int t = w * 32 + l;
+            const int a = P::addr(P::node(G, t, K));
+            if (a < 0 || a >= P::XW) return false;
+            if (P::PAD && a != P::addr(P::tpart(G, t)) + P::addr(P::kpart(G, K))) return false;
+            const uint32_t bit = 1u << (a & 31);
+            if (banks & bit) return false;
+            banks |= bit;
+        }
+    }
+    return true;
+}
+template <class P, int G, int K>
+struct PlanBankCheck {
+    static_assert(plan_group_banks<P, G, K>(), "exchange layout has bank conflicts");
+    static constexpr bool ok = true;
+};
+template <class P, int G, class KS>
+struct PlanGroupCheck;
+template <class P, int G, int... K>
+struct PlanGroupCheck<P, G, std::integer_sequence<int, K...>> {
+    static_assert(plan_group_bijective<P, G>(), "exchange layout: a group does not cover the nodes once");
+    static constexpr bool ok = (PlanBankCheck<P, G, K>::ok && ...);
+};
+template <class P, class GS>
+struct PlanCheck;
+template <class P, int... G>
+struct PlanCheck<P, std::integer_sequence<int, G...>> {
+    static constexpr bool ok = (PlanGroupCheck<P, G, std::make_integer_sequence<int, P::R>>::ok && ...);
+};
 template <class P>
 constexpr bool plan_is_conflict_free()
 {
-    // every group maps (thread, register) onto the N nodes one to one
-    for (int g = 0; g < P::NG; ++g) {
-        uint32_t seen[P::N / 32] = {};
-        for (int t = 0; t < P::T; ++t)
-            for (int k = 0; k < P::R; ++k) {
-                const int j = P::node(g, t, k);
-                if (j < 0 || j >= P::N || ((seen[j >> 5] >> (j & 31)) & 1u)) return false;
-                seen[j >> 5] |= 1u << (j & 31);
-            }
-    }
-    for (int g = 0; g < P::NG; ++g)
-        for (int k = 0; k < P::R; ++k)
-            for (int w = 0; w < P::NW; ++w) {
-                uint32_t banks = 0;
-                for (int l = 0; l < 32 && w * 32 + l < P::T; ++l) {
-                    const int t = w * 32 + l;
-                    const int a = P::addr(P::node(g, t, k));
-                    if (a < 0 || a >= P::XW) return false;
-                    // PAD: the address splits into the thread's base and the register's offset
-                    if (P::PAD && a != P::addr(P::tpart(g, t)) + P::addr(P::kpart(g, k))) return false;
-                    const uint32_t bit = 1u << (a & 31);
-                    if (banks & bit) return false;
-                    banks |= bit;
-                }
-            }
-    return true;
+    return PlanCheck<P, std::make_integer_sequence<int, P::NG>>::ok;
 }
 
 // Exchange-buffer access of register k of thread t in group G: the thread's base of group G
@@ -352,6 +379,10 @@ template <> struct BPConfig<8>  { using Plan = BPPlan<8, 3>;  static constexpr i
 template <> struct BPConfig<9>  { using Plan = BPPlan<9, 3>;  static constexpr int F = 1, MIN_CTAS = 8, MIN_CTAS_W = 5; };
 template <> struct BPConfig<10> { using Plan = BPPlan<10, 3>; static constexpr int F = 1, MIN_CTAS = 4, MIN_CTAS_W = 3; };
 template <> struct BPConfig<11> { using Plan = BPPlan<11, 3>; static constexpr int F = 1, MIN_CTAS = 2, MIN_CTAS_W = 1; };
+// N = 4096: one frame group of 512 threads per SM; the live messages of a thread (about n + 1
+// columns of 8 nodes: the R columns the coming L sweep reads and the L columns the coming R sweep
+// reads) fit its 128 registers, so the frame stays on one SM without a cluster
+template <> struct BPConfig<12> { using Plan = BPPlan<12, 3>; static constexpr int F = 1, MIN_CTAS = 1, MIN_CTAS_W = 1; };
 
 template <class P>
 __host__ __device__ constexpr int bp_slot_words()
@@ -364,7 +395,19 @@ __host__ __device__ constexpr int bp_slot_words()
 // One frame group of T threads decoding frames from `src` until it runs dry.  Group `slot` of
 // the CTA uses the shared-memory slice `slot_smem` (bp_slot_words<P>() words).
 // SYNP (half2 only): both frames' CRC syndromes in one word -- for CRCs of at most 16 bits.
-template <class P, class MSG, bool WEIGHTED, bool SHARED_CTA, class Src, bool SYNP = false>
+// VAR (FP32, unweighted): bit 0 the exact PE function instead of min-sum, bit 1 the re-encoding
+// stop -- the frame stops at the first iteration where HD(LLR(x)) equals the re-encoded HD(LLR(u))
+// (x = u G, Sec. II-B) and counts as decoded iff its CRC then holds.
+template <int R>
+__host__ __device__ constexpr uint32_t pe_low_mask(int dd)
+{
+    uint32_t m = 0;
+    for (int k = 0; k < R; ++k)
+        if (!(k & dd)) m |= 1u << k;
+    return m;
+}
+
+template <class P, class MSG, bool WEIGHTED, bool SHARED_CTA, class Src, bool SYNP = false, int VAR = 0>
 __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, int slot, int t, uint32_t* slot_smem,
                                              Src& src)
 {
@@ -376,6 +419,17 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
     // alternation across iterations, so a buffer is rewritten only after a barrier that follows
     // every read of its previous contents
     static_assert(P::xidx_l(0) % 2 == 0, "odd number of exchanges per iteration");
+    constexpr bool EXACT = (VAR & 1) != 0, REENC = (VAR & 2) != 0;
+    static_assert(VAR == 0 || (FPT == 1 && !WEIGHTED), "exact g and the re-encoding stop: FP32, unweighted");
+    static_assert(!REENC || (T % 32 == 0 && (!SHARED_CTA || T == 32)), "re-encoding vote: whole warps, own barrier");
+    // PE function: min-sum (one instruction) or exact; the exact value is clipped like every
+    // message, since its fast logarithms may overshoot min(|a|, |b|) by an ulp
+    auto gf = [&](MSG x, MSG y) -> MSG {
+        if constexpr (EXACT)
+            return clipm(g_exact(x, y), MT::splat(a.llr_max));
+        else
+            return xmin(x, y);
+    };
 
     MSG* xbuf = reinterpret_cast<MSG*>(slot_smem);         // [2][XW]
     uint32_t* csyn = slot_smem + 2 * P::XW;                // [R][T]
@@ -498,8 +552,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             for (int k = 0; k < R; ++k) {
                 if (k & dd) continue;
                 const int k2 = k | dd;
-                MSG o1 = xmin(Rc[n][k], fadd(Lc[n + 1][k2], Rc[n][k2]));
-                MSG gg = xmin(Rc[n][k], Lc[n + 1][k]);
+                MSG o1 = gf(Rc[n][k], fadd(Lc[n + 1][k2], Rc[n][k2]));
+                MSG gg = gf(Rc[n][k], Lc[n + 1][k]);
                 if constexpr (WEIGHTED) {
                     // itc of this half was already advanced past the last iteration
                     const MSG w1 = MT::splat(wscalar(it_done - 1, 0, n, k));
@@ -538,6 +592,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
         // scales of the stage being computed and of the next one (loaded a stage ahead)
         WPair wc{}, wn{};
         if constexpr (WEIGHTED) wc = wload(0, 1);
+        uint32_t xh = 0;  // re-encoding stop: HD(LLR(x)) of this thread's channel-column nodes
         // ------------------------------------------------------------------ R sweep
         static_for<1, n + 1>([&](auto S) {
             constexpr int s = S.value, q = s - 1, g = P::grp(q), dd = 1 << (q - P::win(g));
@@ -550,13 +605,18 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                 if (k & dd) continue;
                 const int k2 = k | dd;
                 const MSG a1 = Rc[s][k], a2 = Rc[s][k2], l1 = Lc[s + 1][k], l2 = Lc[s + 1][k2];
-                MSG o1 = xmin(a1, fadd(l2, a2));
-                MSG gg = xmin(a1, l1);
+                MSG o1 = gf(a1, fadd(l2, a2));
+                MSG gg = gf(a1, l1);
                 if constexpr (WEIGHTED) {
                     o1 = clipm(fmul(wk(wc, k), o1), Mv);
                     gg = fmul(wk(wc, k2), gg);
                 }
                 const MSG o2 = clipm(fadd(gg, a2), Mv);
+                if constexpr (REENC && last) {
+                    // LLR(x) = L[n+1] + R[n+1]: the channel column plus this stage's output
+                    xh |= (MT::neg(fadd(l1, o1), 0) ? 1u : 0u) << k;
+                    xh |= (MT::neg(fadd(l2, o2), 0) ? 1u : 0u) << k2;
+                }
                 if constexpr (!last) {
                     if constexpr (cross) {
                         xput<P, g>(xb, xbase, t, k, o1);
@@ -587,8 +647,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                 if (k & dd) continue;
                 const int k2 = k | dd;
                 const MSG a1 = Rc[s][k], a2 = Rc[s][k2], l1 = Lc[s + 1][k], l2 = Lc[s + 1][k2];
-                MSG o1 = xmin(l1, fadd(l2, a2));
-                MSG gg = xmin(a1, l1);
+                MSG o1 = gf(l1, fadd(l2, a2));
+                MSG gg = gf(a1, l1);
                 if constexpr (WEIGHTED) {
                     o1 = clipm(fmul(wk(wc, k), o1), Mv);
                     gg = fmul(wk(wc, k2), gg);
@@ -662,6 +722,34 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             syn1 = syn0 >> 16;
             syn0 &= 0xFFFFu;
         }
+        bool conv = false;
+        if constexpr (REENC) {
+            // x = u G by the butterflies of Fig. 1 on the decided bits (stage q XORs node j + 2^q
+            // into node j): in registers within a group's window, through the exchange buffers
+            // between groups (the R sweep's buffers and alternation; the vote below is the barrier
+            // that orders the last exchange's reads before the next iteration's first writes)
+            uint32_t v = 0;
+#pragma unroll
+            for (int k = 0; k < R; ++k) v |= (MT::neg(fadd(Lc[1][k], Rc[1][k]), 0) ? 1u : 0u) << k;
+            static_for<1, n + 1>([&](auto S) {
+                constexpr int s = S.value, q = s - 1, g = P::grp(q), dd = 1 << (q - P::win(g));
+                v ^= (v >> dd) & pe_low_mask<R>(dd);
+                if constexpr (P::rcross(s)) {
+                    uint32_t* xb = reinterpret_cast<uint32_t*>(xbuf + (P::xidx_r(s) & 1) * P::XW);
+#pragma unroll
+                    for (int k = 0; k < R; ++k) xput<P, g>(xb, xbase, t, k, (v >> k) & 1u);
+                    group_sync<T, SHARED_CTA>(slot);
+                    v = 0;
+#pragma unroll
+                    for (int k = 0; k < R; ++k) v |= xget<P, P::grp(s)>(xb, xbase, t, k) << k;
+                }
+            });
+            // v now holds the re-encoded bits of this thread's channel-column nodes, as xh does
+            if constexpr (T == 32)
+                conv = !__any_sync(0xffffffffu, v != xh);
+            else
+                conv = !__syncthreads_or(v != xh);
+        }
         ++it;
         const uint32_t syn[2] = {syn0, syn1};
         bool any = false;
@@ -670,7 +758,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             if (fr[h] < 0) continue;
             ++itc[h];
             const bool ok = syn[h] == 0u;
-            if ((ok && !a.fixed_iters) || itc[h] >= a.max_iters) {
+            const bool stop = REENC ? conv : ok;
+            if ((stop && !a.fixed_iters) || itc[h] >= a.max_iters) {
                 finalize(h, itc[h], ok);
                 refill(h);
             }
@@ -682,7 +771,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 
 // Per-length kernel: F frame groups per CTA; THREADS = F * T (passed explicitly: launch bounds
 // take no dependent member expression).
-template <int LOGN, class MSG, bool WEIGHTED, int THREADS, bool SYNP = false>
+template <int LOGN, class MSG, bool WEIGHTED, int THREADS, bool SYNP = false, int VAR = 0>
 __global__ void __launch_bounds__(THREADS, WEIGHTED ? BPConfig<LOGN>::MIN_CTAS_W : BPConfig<LOGN>::MIN_CTAS) bp_kernel(const BPArgs a)
 {
     using P = typename BPConfig<LOGN>::Plan;
@@ -694,8 +783,8 @@ __global__ void __launch_bounds__(THREADS, WEIGHTED ? BPConfig<LOGN>::MIN_CTAS_W
     const int t = threadIdx.x % P::T;
     constexpr int FPT = MsgTraits<MSG>::FPT;
     CounterSource src{a.next, a.B, (int)((blockIdx.x * F + slot) * FPT), FPT, a.frame0};
-    bp_run_group<P, MSG, WEIGHTED, false, CounterSource, SYNP>(a, *a.code, slot, t, smem + slot * bp_slot_words<P>(),
-                                                               src);
+    bp_run_group<P, MSG, WEIGHTED, false, CounterSource, SYNP, VAR>(a, *a.code, slot, t,
+                                                                    smem + slot * bp_slot_words<P>(), src);
 }
 
 }  // namespace polar

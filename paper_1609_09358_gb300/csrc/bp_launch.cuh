@@ -16,6 +16,8 @@ struct BPKernelInfo {
 // kernel of (log2 N, weighted) for the message type of this translation unit; half2 plain
 // kernels come in a variant with both frames' CRC syndromes in one word (crc_len <= 16)
 BPKernelInfo bp_kernel_info_fp32(int logn, bool weighted);
+// FP32 unweighted kernel of a BP variant: bit 0 exact PE function, bit 1 re-encoding stop
+BPKernelInfo bp_kernel_info_fp32_var(int logn, int var);
 BPKernelInfo bp_kernel_info_fp16(int logn, bool weighted, bool packed_syndrome);
 // natural-layout learned weights [iters][2][n][N] -> the prepared layout of the length's plan
 cudaError_t wms_prepare_fp32(int logn, const float* w, int iters, void* out, cudaStream_t st);
@@ -52,9 +54,14 @@ BPKernelInfo bp_kernel_info_t(int logn, bool weighted, bool packed_syndrome = fa
         constexpr int TH = Cfg::F * P::T;
         const size_t smem = (size_t)Cfg::F * bp_slot_words<P>() * 4;
         const void* fn;
-        if (weighted)
-            fn = (const void*)bp_kernel<LOGN, MSG, true, TH>;
-        else if constexpr (std::is_same<MSG, __half2>::value)
+        if (weighted) {
+            // learned weights: N <= 2048 (no weighted kernel is built for longer codes)
+            if constexpr (LOGN > 11)
+                return BPKernelInfo{nullptr, TH, smem, Cfg::F};
+            else
+                return BPKernelInfo{(const void*)bp_kernel<LOGN, MSG, true, TH>, TH, smem, Cfg::F};
+        }
+        if constexpr (std::is_same<MSG, __half2>::value)
             fn = packed_syndrome ? (const void*)bp_kernel<LOGN, MSG, false, TH, true>
                                  : (const void*)bp_kernel<LOGN, MSG, false, TH>;
         else
@@ -66,7 +73,29 @@ BPKernelInfo bp_kernel_info_t(int logn, bool weighted, bool packed_syndrome = fa
         case 8: return pick(std::integral_constant<int, 8>{});
         case 9: return pick(std::integral_constant<int, 9>{});
         case 10: return pick(std::integral_constant<int, 10>{});
-        default: return pick(std::integral_constant<int, 11>{});
+        case 11: return pick(std::integral_constant<int, 11>{});
+        default: return pick(std::integral_constant<int, 12>{});
+    }
+}
+
+template <int VAR>
+BPKernelInfo bp_kernel_info_var_t(int logn)
+{
+    auto pick = [&](auto LOGN_C) -> BPKernelInfo {
+        constexpr int LOGN = decltype(LOGN_C)::value;
+        using Cfg = BPConfig<LOGN>;
+        using P = typename Cfg::Plan;
+        constexpr int TH = Cfg::F * P::T;
+        const size_t smem = (size_t)Cfg::F * bp_slot_words<P>() * 4;
+        return {(const void*)bp_kernel<LOGN, float, false, TH, false, VAR>, TH, smem, Cfg::F};
+    };
+    switch (logn) {
+        case 7: return pick(std::integral_constant<int, 7>{});
+        case 8: return pick(std::integral_constant<int, 8>{});
+        case 9: return pick(std::integral_constant<int, 9>{});
+        case 10: return pick(std::integral_constant<int, 10>{});
+        case 11: return pick(std::integral_constant<int, 11>{});
+        default: return pick(std::integral_constant<int, 12>{});
     }
 }
 

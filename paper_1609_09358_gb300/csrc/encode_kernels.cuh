@@ -6,11 +6,12 @@
 
 namespace polar {
 
-// One warp per frame.  Lane l owns the 32-bit words l and l + 32 of the N-bit vectors (N <= 2048).
+// One warp per frame.  Lane l owns the 32-bit words l + 32 h (h < kMaxWords / 32) of the N-bit
+// vectors.
 // CRC: XOR of the syndrome columns x^(K-1-k) mod g of the payload bits set (k < P), which is the
 // remainder of payload(x) x^c; its bits go to the last c information positions, MSB first.
 // Transform: the Fig. 1 butterflies x_j ^= x_{j+d} (bit log2 d of j clear) -- in-word with shifts
-// for d < 32, across words with shuffles for 32 <= d < 1024 and within the lane for d = 1024.
+// for d < 32, across words with shuffles for 32 <= d < 1024 and within the lane for d >= 1024.
 __global__ void encode_kernel(const DevCode* __restrict__ code, const uint8_t* __restrict__ payload,
                               int B, int pay_bytes, uint8_t* __restrict__ codeword)
 {
@@ -24,9 +25,12 @@ __global__ void encode_kernel(const DevCode* __restrict__ code, const uint8_t* _
     for (int p = lane; p < P; p += 32)
         if ((pay[p >> 3] >> (p & 7)) & 1) crc ^= C.colsyn[C.info_idx[p]];
     crc = __reduce_xor_sync(0xffffffffu, crc);
-    uint32_t w[2] = {0u, 0u};
+    constexpr int H = kMaxWords / 32;
+    uint32_t w[H];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < H; ++h) w[h] = 0u;
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
         const int wi = lane + 32 * h;
         if (wi >= words) break;
         uint32_t v = 0;
@@ -50,20 +54,24 @@ __global__ void encode_kernel(const DevCode* __restrict__ code, const uint8_t* _
     (void)K;
     const uint32_t m[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int h = 0; h < H; ++h)
 #pragma unroll
         for (int e = 0; e < 5; ++e) w[h] ^= (w[h] >> (1 << e)) & m[e];
     for (int D = 1; D < 32 && D < words; D <<= 1) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < H; ++h) {
             const uint32_t other = __shfl_xor_sync(0xffffffffu, w[h], D);
             if (!(lane & D)) w[h] ^= other;
         }
     }
-    if (words > 32) w[0] ^= w[1];
+#pragma unroll
+    for (int hd = 1; hd < H; hd <<= 1)
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+            if (!(h & hd) && 32 * (h | hd) < words) w[h] ^= w[h | hd];
     uint8_t* out = codeword + (size_t)frame * (N >> 3);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < H; ++h) {
         const int wi = lane + 32 * h;
         if (wi < words) reinterpret_cast<uint32_t*>(out)[wi] = w[h];
     }

@@ -2,12 +2,14 @@
 // cache, workspace layout and kernel dispatch.  Every decoding step runs in the kernels of
 // bp_kernel.cuh, scl_kernel.cuh and encode_kernels.cuh; nothing here touches frame data.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "bp_launch.cuh"
@@ -223,6 +225,18 @@ static HostSet host_set_layout(const polar_code* code, int B, int L)
     return h;
 }
 
+// Per-chunk counters of hybrid_decode_scheduled (chunks of at least kSchedMinChunk frames).
+struct SchedHdr {
+    int fail_count;
+    int scl_next;
+    int pad[2];
+};
+constexpr int kSchedMinChunk = 256;
+static size_t sched_hdr_bytes(int B)
+{
+    return align_up(sizeof(SchedHdr) * (size_t)((std::max(B, 1) + kSchedMinChunk - 1) / kSchedMinChunk), 256);
+}
+
 static size_t ws_bytes(const polar_code* code, int B, int L, int op)
 {
     if (op == POLAR_OP_BP) return 0;
@@ -231,13 +245,17 @@ static size_t ws_bytes(const polar_code* code, int B, int L, int op)
     if (op == POLAR_OP_HYBRID) {
         b += hybrid_chunk_header_bytes(B);
         b += align_up(sizeof(int) * (size_t)std::max(B, 1), 256);
+    } else if (op == POLAR_OP_HYBRID_SCHED) {
+        b += sched_hdr_bytes(B);
+        b += align_up(sizeof(int) * (size_t)std::max(B, 1), 256);
     }
     b += scl_scratch_bytes(code->N, L);
     return b;
 }
 
-// library-owned streams per device for hybrid_decode_host: [0] a second compute stream, [1] the
-// copy stream
+// library-owned streams per device: hybrid_decode_host's second compute stream [0] and copy stream
+// [1]; hybrid_decode_scheduled's BP streams [2 .. 2 + POLAR_SCHED_BP_STREAMS) and CA-SCL stream
+constexpr int kAuxStreams = 3 + POLAR_SCHED_BP_STREAMS;
 static std::mutex g_aux_mutex;
 static std::vector<cudaStream_t> g_aux;
 static int aux_stream(int which, cudaStream_t* out)
@@ -245,8 +263,8 @@ static int aux_stream(int which, cudaStream_t* out)
     int dev = 0;
     POLAR_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(g_aux_mutex);
-    if ((int)g_aux.size() <= 2 * dev + which) g_aux.resize(2 * dev + 2, nullptr);
-    cudaStream_t& sref = g_aux[2 * dev + which];
+    if ((int)g_aux.size() <= kAuxStreams * dev + which) g_aux.resize(kAuxStreams * (dev + 1), nullptr);
+    cudaStream_t& sref = g_aux[kAuxStreams * dev + which];
     if (!sref) POLAR_CUDA(cudaStreamCreateWithFlags(&sref, cudaStreamNonBlocking));
     *out = sref;
     return POLAR_OK;
@@ -300,6 +318,13 @@ struct ProfScope {
     }
 };
 
+// BP variant bits carried in `precision` (bit 0 exact g, bit 1 re-encoding stop) and the message type
+static int bp_variant(int precision)
+{
+    return ((precision & POLAR_G_EXACT) ? 1 : 0) | ((precision & POLAR_STOP_REENCODE) ? 2 : 0);
+}
+static int bp_message(int precision) { return precision & ~(POLAR_G_EXACT | POLAR_STOP_REENCODE); }
+
 static int launch_bp(const DevCode* dcode, const polar_code* code, const float* llr, int B, int max_iters,
                      float llr_max, int precision, const void* w, int w_iters, uint8_t* bits, uint8_t* status,
                      uint16_t* iters, float* llr_u, float* llr_x, int* fail_count, int* fail_list,
@@ -328,9 +353,25 @@ static int launch_bp(const DevCode* dcode, const polar_code* code, const float* 
     a.row_bytes = (code->K - code->crc_len + 7) / 8;
     const int n = log2i(code->N);
     if (B == 0) return POLAR_OK;
-    if (n < 7 || n > 11) return fail(POLAR_ERR_ARG, "unsupported N = %d", code->N);
+    if (n < 7 || n > 12) return fail(POLAR_ERR_ARG, "unsupported N = %d", code->N);
+    if (w && code->N > POLAR_MAX_N_MIXED)
+        return fail(POLAR_ERR_ARG, "learned weights: N = %d > %d", code->N, POLAR_MAX_N_MIXED);
+    const int var = bp_variant(precision);
+    precision = bp_message(precision);
     const BPKernelInfo k = precision == POLAR_FP16 ? bp_kernel_info_fp16(n, w != nullptr, code->crc_len <= 16)
-                                                   : bp_kernel_info_fp32(n, w != nullptr);
+                           : var               ? bp_kernel_info_fp32_var(n, var)
+                                               : bp_kernel_info_fp32(n, w != nullptr);
+    if (!k.fn) return fail(POLAR_ERR_ARG, "no BP kernel for N = %d with these options", code->N);
+    if (k.smem > 48 * 1024) {
+        // above the default dynamic shared-memory limit (N = 4096); set once per kernel
+        static std::mutex m;
+        static std::vector<const void*> done;
+        std::lock_guard<std::mutex> lock(m);
+        if (std::find(done.begin(), done.end(), k.fn) == done.end()) {
+            POLAR_CUDA(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
+            done.push_back(k.fn);
+        }
+    }
     const int fpt = precision == POLAR_FP16 ? 2 : 1;
     const int groups = (B + fpt - 1) / fpt;
     const int F = k.groups_per_cta;
@@ -354,6 +395,9 @@ static int check_bp_args(const polar_code* code, const float* llr, int B, int ma
 {
     const int rc = check_code(code);
     if (rc) return rc;
+    if (bp_variant(precision) && (bp_message(precision) != POLAR_FP32 || w))
+        return fail(POLAR_ERR_ARG, "POLAR_G_EXACT / POLAR_STOP_REENCODE need POLAR_FP32 messages and no learned weights");
+    precision = bp_message(precision);
     if (B < 0) return fail(POLAR_ERR_ARG, "B = %d < 0", B);
     if (max_iters < 1 || max_iters > 65535) return fail(POLAR_ERR_ARG, "max_iters = %d: must be in [1, 65535]", max_iters);
     if (!(llr_max > 0.0f) || !std::isfinite(llr_max)) return fail(POLAR_ERR_ARG, "llr_max must be finite and > 0");
@@ -510,7 +554,7 @@ size_t polar_workspace_bytes(const polar_code* code, int32_t B, int32_t L, int32
 {
     if (check_code(code) != POLAR_OK || B < 0) return 0;
     if (op != POLAR_OP_BP && !valid_L(L)) return 0;
-    if (op < POLAR_OP_BP || op > POLAR_OP_HYBRID_HOST) return 0;
+    if (op < POLAR_OP_BP || op > POLAR_OP_HYBRID_SCHED) return 0;
     return ws_bytes(code, B, L, op);
 }
 
@@ -652,9 +696,137 @@ int hybrid_decode_host(const polar_code* code, const float* llr_host, int32_t B,
     return rc;
 }
 
+// page-locked host copies of the chunks' failure counts (hybrid_decode_scheduled; calls serialise)
+static std::mutex g_sched_mutex;
+static int* g_sched_counts = nullptr;
+static size_t g_sched_cap = 0;
+
+int hybrid_decode_scheduled(const polar_code* code, const float* llr, int32_t B, int32_t max_iters, float llr_max,
+                            int32_t precision, const void* wms_scales, int32_t wms_iters, int32_t L, int32_t chunk,
+                            uint8_t* bits, uint8_t* status, uint16_t* iters, void* workspace, size_t ws, void* stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_bp_args(code, llr, B, max_iters, llr_max, precision, wms_scales, wms_iters, bits, status, iters);
+    if (rc) return rc;
+    if (!valid_L(L)) return fail(POLAR_ERR_ARG, "L = %d: must be 1, 2, 4, 8, 16 or 32", L);
+    if (chunk < kSchedMinChunk) return fail(POLAR_ERR_ARG, "chunk = %d: must be >= %d", chunk, kSchedMinChunk);
+    const DevCode* d = nullptr;
+    if ((rc = code_slot(code, st, &d))) return rc;
+    if (B == 0) return POLAR_OK;
+    const size_t need = ws_bytes(code, B, L, POLAR_OP_HYBRID_SCHED);
+    if (!workspace || ws < need) return fail(POLAR_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws, need);
+    char* base = static_cast<char*>(workspace);
+    SchedHdr* hdr = reinterpret_cast<SchedHdr*>(base + kHeaderBytes);
+    int* list = reinterpret_cast<int*>(base + kHeaderBytes + sched_hdr_bytes(B));
+    void* scratch = reinterpret_cast<char*>(list) + align_up(sizeof(int) * (size_t)B, 256);
+    const int nchunks = (B + chunk - 1) / chunk;
+    constexpr int S = POLAR_SCHED_BP_STREAMS;
+    cudaStream_t sbp[S], sscl = nullptr;
+    for (int i = 0; i < S; ++i)
+        if ((rc = aux_stream(2 + i, &sbp[i]))) return rc;
+    if ((rc = aux_stream(2 + S, &sscl))) return rc;
+
+    std::lock_guard<std::mutex> lock(g_sched_mutex);
+    if (g_sched_cap < (size_t)nchunks) {
+        if (g_sched_counts) cudaFreeHost(g_sched_counts);
+        g_sched_counts = nullptr;
+        g_sched_cap = 0;
+        POLAR_CUDA(cudaMallocHost(&g_sched_counts, sizeof(int) * (size_t)nchunks));
+        g_sched_cap = (size_t)nchunks;
+    }
+    struct Events {
+        std::vector<cudaEvent_t> v;
+        ~Events()
+        {
+            for (cudaEvent_t e : v) cudaEventDestroy(e);
+        }
+    } evs;
+    auto event = [&](cudaEvent_t* e) -> int {
+        POLAR_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        evs.v.push_back(*e);
+        return POLAR_OK;
+    };
+    cudaEvent_t ev0 = nullptr, ev_scl = nullptr, ev_bp[S];
+    if ((rc = event(&ev0)) || (rc = event(&ev_scl))) return rc;
+    for (int i = 0; i < S; ++i)
+        if ((rc = event(&ev_bp[i]))) return rc;
+    POLAR_CUDA(cudaMemsetAsync(hdr, 0, sizeof(SchedHdr) * (size_t)nchunks, st));
+    POLAR_CUDA(cudaEventRecord(ev0, st));
+    for (int i = 0; i < S; ++i) POLAR_CUDA(cudaStreamWaitEvent(sbp[i], ev0, 0));
+    POLAR_CUDA(cudaStreamWaitEvent(sscl, ev0, 0));
+
+    int slot[S];  // chunk in BP on each stream, -1 = free
+    bool used[S];
+    for (int i = 0; i < S; ++i) slot[i] = -1, used[i] = false;
+    std::vector<int> waiting;  // chunks whose failed frames wait for CA-SCL
+    bool scl_busy = false, scl_used = false;
+    int next = 0, done = 0;
+    using clock = std::chrono::steady_clock;
+    auto last_progress = clock::now();
+    while (rc == POLAR_OK && (done < nchunks || !waiting.empty())) {
+        bool progress = false;
+        // enough buffer space: start the next chunks' BP on free streams
+        for (int i = 0; i < S && next < nchunks && rc == POLAR_OK; ++i) {
+            if (slot[i] >= 0) continue;
+            const int c = next++, b0 = c * chunk, nb = std::min(chunk, B - b0);
+            rc = launch_bp(d, code, llr, nb, max_iters, llr_max, precision, wms_scales, wms_iters, bits, status,
+                           iters, nullptr, nullptr, &hdr[c].fail_count, list + b0, sbp[i], nullptr, nullptr, 0, b0);
+            if (rc) break;
+            POLAR_CUDA(cudaMemcpyAsync(&g_sched_counts[c], &hdr[c].fail_count, sizeof(int), cudaMemcpyDeviceToHost,
+                                       sbp[i]));
+            POLAR_CUDA(cudaEventRecord(ev_bp[i], sbp[i]));
+            slot[i] = c;
+            used[i] = progress = true;
+        }
+        if (rc) break;
+        // BP finished: its chunk's failures (counted on the device) wait for CA-SCL
+        for (int i = 0; i < S; ++i) {
+            if (slot[i] < 0) continue;
+            const cudaError_t e = cudaEventQuery(ev_bp[i]);
+            if (e == cudaErrorNotReady) continue;
+            if (e != cudaSuccess) return cuda_fail(e, "BP launch of a chunk");
+            if (g_sched_counts[slot[i]] > 0) waiting.push_back(slot[i]);
+            slot[i] = -1;
+            ++done;
+            progress = true;
+        }
+        // failures waiting and the CA-SCL stream idle: start CA-SCL on every waiting chunk
+        if (!waiting.empty()) {
+            if (scl_busy) {
+                const cudaError_t e = cudaEventQuery(ev_scl);
+                if (e != cudaSuccess && e != cudaErrorNotReady) return cuda_fail(e, "CA-SCL launch");
+                scl_busy = e == cudaErrorNotReady;
+            }
+            if (!scl_busy) {
+                for (int c : waiting) {
+                    rc = launch_scl(d, code, llr, B, L, bits, status, list + (size_t)c * chunk, &hdr[c].fail_count,
+                                    &hdr[c].scl_next, scratch, sscl);
+                    if (rc) break;
+                }
+                waiting.clear();
+                POLAR_CUDA(cudaEventRecord(ev_scl, sscl));
+                scl_busy = scl_used = progress = true;
+            }
+        }
+        if (progress) {
+            last_progress = clock::now();
+        } else {
+            if (clock::now() - last_progress > std::chrono::seconds(600))
+                return fail(POLAR_ERR_TIMEOUT, "hybrid_decode_scheduled: no launch finished in 600 s");
+            std::this_thread::yield();
+        }
+    }
+    if (rc) return rc;
+    // later work on `stream` follows every launch of the call
+    if (scl_used) POLAR_CUDA(cudaStreamWaitEvent(st, ev_scl, 0));
+    for (int i = 0; i < S; ++i)
+        if (used[i]) POLAR_CUDA(cudaStreamWaitEvent(st, ev_bp[i], 0));
+    return POLAR_OK;
+}
+
 size_t wms_prepared_bytes(const polar_code* code, int32_t wms_iters, int32_t precision)
 {
-    if (check_code(code) != POLAR_OK || wms_iters < 1) return 0;
+    if (check_code(code) != POLAR_OK || wms_iters < 1 || code->N > POLAR_MAX_N_MIXED) return 0;
     if (precision != POLAR_FP32 && precision != POLAR_FP16) return 0;
     const size_t elem = precision == POLAR_FP16 ? 2 : 4;
     return (size_t)wms_iters * 2 * log2i(code->N) * code->N * elem;
@@ -668,7 +840,8 @@ int wms_prepare(const polar_code* code, const float* w, int32_t wms_iters, int32
     if (wms_iters < 1) return fail(POLAR_ERR_ARG, "wms_iters = %d < 1", wms_iters);
     if (precision != POLAR_FP32 && precision != POLAR_FP16) return fail(POLAR_ERR_ARG, "precision = %d", precision);
     const int n = log2i(code->N);
-    if (n < 7 || n > 11) return fail(POLAR_ERR_ARG, "unsupported N = %d", code->N);
+    if (n < 7 || code->N > POLAR_MAX_N_MIXED) return fail(POLAR_ERR_ARG, "learned weights: N = %d > %d", code->N,
+                                                          POLAR_MAX_N_MIXED);
     if (!w || !prepared) return fail(POLAR_ERR_ARG, "NULL weights or output");
     if (reinterpret_cast<uintptr_t>(prepared) & 15u) return fail(POLAR_ERR_ARG, "output not 16-byte aligned");
     const size_t need = wms_prepared_bytes(code, wms_iters, precision);
@@ -681,7 +854,7 @@ int wms_prepare(const polar_code* code, const float* w, int32_t wms_iters, int32
 
 size_t wms_workspace_bytes(const polar_code* code, int32_t B, int32_t T)
 {
-    if (check_code(code) != POLAR_OK || B < 0 || T < 1) return 0;
+    if (check_code(code) != POLAR_OK || B < 0 || T < 1 || code->N > POLAR_MAX_N_MIXED) return 0;
     const size_t n = (size_t)log2i(code->N), N = (size_t)code->N;
     return (size_t)B * (2 * (size_t)T * n * N + 3 * (n + 2) * N) * sizeof(float);
 }
@@ -691,6 +864,7 @@ static int wms_common(const polar_code* code, const float* llr, int B, int T, fl
 {
     int rc = check_code(code);
     if (rc) return rc;
+    if (code->N > POLAR_MAX_N_MIXED) return fail(POLAR_ERR_ARG, "training: N = %d > %d", code->N, POLAR_MAX_N_MIXED);
     if (B < 0 || T < 1 || T > 1000) return fail(POLAR_ERR_ARG, "B = %d, T = %d", B, T);
     if (!(llr_max > 0.0f)) return fail(POLAR_ERR_ARG, "llr_max must be > 0");
     if (B > 0 && (!llr || !w)) return fail(POLAR_ERR_ARG, "NULL llr/w");
@@ -787,6 +961,8 @@ int mix_check(const polar_code* codes, int ncodes, int B, int L, int row_stride,
     for (int c = 0; c < ncodes; ++c) {
         int rc = check_code(&codes[c]);
         if (rc) return rc;
+        if (codes[c].N > POLAR_MAX_N_MIXED)
+            return fail(POLAR_ERR_ARG, "mixed batches: N = %d > %d", codes[c].N, POLAR_MAX_N_MIXED);
         mr = std::max(mr, (codes[c].K - codes[c].crc_len + 7) / 8);
         if (L > 0) {
             const SCLPlan p = scl_plan(codes[c].N, L, false);
@@ -894,6 +1070,7 @@ int hybrid_decode_mixed(const polar_code* codes, int32_t ncodes, const int32_t* 
     if (!valid_L(L)) return fail(POLAR_ERR_ARG, "L = %d: must be 1, 2, 4, 8, 16 or 32", L);
     int rc = mix_check(codes, ncodes, B, L, row_stride, &mr, &ww, &sw);
     if (rc) return rc;
+    if (bp_variant(precision)) return fail(POLAR_ERR_ARG, "mixed batches decode with min-sum and the CRC stop");
     if ((rc = check_bp_args(&codes[0], llr, B, max_iters, llr_max, precision, nullptr, 0, bits, status, iters))) return rc;
     if (B > 0 && (!code_of || !llr_off || !bits)) return fail(POLAR_ERR_ARG, "NULL code_of/llr_off/bits");
     const DevCode* dcodes[POLAR_MAX_MIX_CODES];
@@ -940,6 +1117,7 @@ int polar_mixed_autotune(const polar_code* codes, int32_t ncodes, const int32_t*
     int mr = 0;
     int rc = mix_check(codes, ncodes, B, 0, row_stride, &mr, nullptr, nullptr);
     if (rc) return rc;
+    if (bp_variant(precision)) return fail(POLAR_ERR_ARG, "mixed batches decode with min-sum and the CRC stop");
     if ((rc = check_bp_args(&codes[0], llr, B, max_iters, llr_max, precision, nullptr, 0, bits, status, iters))) return rc;
     if (B < 1 || !code_of || !llr_off || !bits) return fail(POLAR_ERR_ARG, "autotune needs a non-empty batch");
     const DevCode* dcodes[POLAR_MAX_MIX_CODES];

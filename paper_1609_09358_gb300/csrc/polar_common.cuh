@@ -51,6 +51,19 @@ __device__ __forceinline__ float stage_clip(float v, float m)
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 
+// Exact PE function g(a, b) = ln((1 + e^(a+b)) / (e^a + e^b)) (Sec. II-B), in the form
+//   sign(a) sign(b) min(|a|, |b|) + ln(1 + e^-|a+b|) - ln(1 + e^-|a-b|)
+// (the same function: the LLR of the XOR of two independent bits), whose exponentials never
+// overflow.  The two corrections use the fast exponential and logarithm (absolute error of a few
+// 1e-7 on the clipped magnitudes), so results agree with the exact value to a tolerance, not to
+// the bit.
+__device__ __forceinline__ float g_exact(float a, float b)
+{
+    const float cs = __logf(fadd(1.0f, __expf(-fabsf(fadd(a, b)))));
+    const float cd = __logf(fadd(1.0f, __expf(-fabsf(__fsub_rn(a, b)))));
+    return fadd(xmin(a, b), __fsub_rn(cs, cd));
+}
+
 // ---------------------------------------------------------------------------- half2 primitives
 __device__ __forceinline__ __half2 xmin(__half2 a, __half2 b)
 {

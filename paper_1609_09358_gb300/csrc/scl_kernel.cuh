@@ -130,15 +130,21 @@ inline size_t scl_scratch_bytes(int N, int L)
     return (size_t)scl_sm_count() * kSclWarpsPerSM * (size_t)w * 4;
 }
 
-__device__ __forceinline__ uint32_t fld(const uint32_t (&w)[2], int k) { return ((k < 6 ? w[0] : w[1]) >> (5 * (k % 6))) & 31u; }
+// 5-bit pointer of upper level k (5 <= k <= 12) in a path's two pointer words: levels 1..6 in word
+// 0, levels 7..12 in word 1
+__device__ __forceinline__ uint32_t fld(const uint32_t (&w)[2], int k)
+{
+    return (k <= 6 ? w[0] >> (5 * (k - 1)) : w[1] >> (5 * (k - 7))) & 31u;
+}
 __device__ __forceinline__ void set_fld(uint32_t (&w)[2], int k, uint32_t v)
 {
-    const int s = 5 * (k % 6);
-    if (k < 6)
+    const int s = 5 * (k <= 6 ? k - 1 : k - 7);
+    if (k <= 6)
         w[0] = (w[0] & ~(31u << s)) | (v << s);
     else
         w[1] = (w[1] & ~(31u << s)) | (v << s);
 }
+static_assert(kMaxN <= 4096, "upper-level pointers of levels up to 12");
 
 // Lanes of one list: the whole warp (W = 32, one frame per warp) or one half of it (W = 16, two
 // frames per warp, lists of at most 8 paths).  Path p of the list sits in lane base + p.  Every
@@ -718,7 +724,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
     // ------------------------------------------------------------------ CRC selection
     // u = x G on each path's N-bit codeword (level-n array), in place; syndrome of its
     // information bits.  The list's lanes hold the codeword's 32-bit words lane + W h.
-    constexpr int H = 64 / W;  // words per lane for N <= 2048
+    constexpr int H = kMaxWords / W;  // words per lane
     const int words = N >> 5;
     uint32_t* xl = S.Cl(n);
     const uint32_t my_x = fld(pC, n);

@@ -65,6 +65,33 @@ def test_argument_errors_without_gpu(lib):
     assert lib.polar_workspace_bytes(good.ref(), 10, 3, 1) == 0
 
 
+def test_bp_variant_flags_are_checked(lib):
+    """The exact g and the re-encoding stop are FP32, unweighted, single-code variants: other uses
+    are rejected before anything reaches the device."""
+    good = api.PolarCode(128, 64, 8, oracle.make_code(128, 64, 8).frozen)
+    for flags in (api.POLAR_G_EXACT, api.POLAR_STOP_REENCODE, api.POLAR_G_EXACT | api.POLAR_STOP_REENCODE):
+        rc = lib.bp_decode(good.ref(), None, 4, 10, 20.0, api.POLAR_FP16 | flags, None, 0, None, None, None, None,
+                           None, None, 0, None)
+        assert rc == -1 and "POLAR_FP32" in lib.polar_last_error().decode()
+        w = ctypes.c_void_p(64)  # never dereferenced: the flag check comes first
+        rc = lib.hybrid_decode(good.ref(), None, 4, 10, 20.0, flags, w, 20, 8, None, None, None, None, 0, None)
+        assert rc == -1 and "learned weights" in lib.polar_last_error().decode()
+        codes = (api._PolarCode * 1)(good._c)
+        rc = lib.hybrid_decode_mixed(codes, 1, None, None, None, 4, 10, 20.0, flags, 8, None, 16, None, None, None,
+                                     0, None)
+        assert rc == -1 and "mixed" in lib.polar_last_error().decode()
+
+
+def test_scheduled_arguments_without_gpu(lib):
+    good = api.PolarCode(128, 64, 8, oracle.make_code(128, 64, 8).frozen)
+    rc = lib.hybrid_decode_scheduled(good.ref(), None, 0, 10, 20.0, 0, None, 0, 8, 255, None, None, None, None, 0,
+                                     None)
+    assert rc == -1 and "chunk" in lib.polar_last_error().decode()
+    assert lib.polar_workspace_bytes(good.ref(), 1000, 8, api.POLAR_OP_HYBRID_SCHED) >= \
+        lib.polar_workspace_bytes(good.ref(), 1000, 8, api.POLAR_OP_HYBRID)
+    assert lib.polar_workspace_bytes(good.ref(), 1000, 8, 5) == 0
+
+
 def test_bit_packing_roundtrip():
     rng = np.random.default_rng(0)
     b = rng.integers(0, 2, (5, 61), dtype=np.uint8)

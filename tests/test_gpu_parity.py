@@ -67,6 +67,8 @@ BP_CASES = [
     (2048, 1024, 24, 1.5, 9, 80),
     (1024, 768, 16, 3.0, 21, 100),
     (256, 64, 16, 1.0, 33, 40),
+    (4096, 2048, 16, 2.0, 7, 50),    # the paper's length: one 512-thread frame group per SM
+    (4096, 2048, 16, 1.0, 3, 50),
 ]
 
 
@@ -79,7 +81,8 @@ def test_bp_fp32_bit_exact(N, K, crc, ebn0, B, imax):
     assert_bp_equal(got, ref, ocode)
 
 
-@pytest.mark.parametrize("N,K,crc,ebn0,B,imax", [c for c in BP_CASES if c[0] <= 1024][:6] + [(2048, 1024, 24, 1.5, 9, 80)])
+@pytest.mark.parametrize("N,K,crc,ebn0,B,imax", [c for c in BP_CASES if c[0] <= 1024][:6] + [(2048, 1024, 24, 1.5, 9, 80),
+                                                                                              (4096, 2048, 16, 2.0, 9, 50)])
 def test_bp_fp16_bit_exact_vs_binary16_emulation(N, K, crc, ebn0, B, imax):
     ocode = fr.oracle_code(N, K, crc)
     _, llr = fr.frames(ocode, ebn0, B, seed=2000 + N + K)
@@ -212,6 +215,8 @@ SCL_CASES = [
     (512, 256, 16, 1.0, 10, 16),
     (1024, 512, 16, 1.0, 12, 8),
     (2048, 1024, 24, 1.0, 4, 8),
+    (4096, 2048, 16, 1.5, 3, 32),   # the paper's configuration
+    (4096, 2048, 16, 1.5, 5, 8),
 ]
 
 
@@ -252,6 +257,7 @@ def run_hybrid(ocode, llr, imax, L, llr_max=20.0, precision=api.POLAR_FP32):
     (1024, 512, 16, 2.0, 160, 200, 8),
     (1024, 512, 16, 1.0, 24, 30, 8),
     (512, 256, 16, 1.5, 70, 40, 16),
+    (4096, 2048, 16, 1.5, 12, 50, 32),  # the paper's configuration, min-sum BP
 ])
 def test_hybrid_bit_exact(N, K, crc, ebn0, B, imax, L):
     ocode = fr.oracle_code(N, K, crc)
@@ -287,7 +293,7 @@ def test_hybrid_full_size_sampled():
 
 
 def test_encoder_bit_exact():
-    for N, K, crc in [(128, 64, 8), (256, 100, 16), (1024, 512, 16), (2048, 1024, 24), (512, 24, 24)]:
+    for N, K, crc in [(128, 64, 8), (256, 100, 16), (1024, 512, 16), (2048, 1024, 24), (512, 24, 24), (4096, 2048, 16)]:
         ocode = fr.oracle_code(N, K, crc, design_rate=K / N)
         code = fr.api_code(ocode)
         from paper_1609_09358_gb300 import inputs
