@@ -838,16 +838,17 @@ def run_paper(a, world, rank, local):
                  "avg_bp_iters": float(it.mean()), "bp_ms_per_step": bp_ms / steps, "scl_ms_per_step": scl_ms / steps,
                  "batch_latency_ms": {"mean": float(np.mean(lat)), "max": float(np.max(lat))}, "clocks": clocks}
             if name == "exact_g":
-                # the exact PE function is bound by the special-function units: 4 of their operations
-                # (2 exponentials, 2 logarithms) per g, 2 n N g per frame-iteration, against
-                # SMs x 16 per clock (compute capability 10.x) x clock
-                ops = 4.0 * 2 * code.n * N * float(it.sum()) * steps
-                peak = sms * 16 * sm_max_mhz * 1e6
+                # the exact PE function is bound by the special-function units: each g takes two
+                # exponentials (32 per clock per SM on this part) and two logarithms (16 per clock),
+                # i.e. at most 16/3 g per clock per SM; 2 n N g per frame-iteration
+                ops = 2.0 * code.n * N * float(it.sum()) * steps
+                peak = sms * (16.0 / 3.0) * sm_max_mhz * 1e6
                 ach = ops / (bp_ms * 1e-3) if bp_ms > 0 else 0.0
-                r["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "Top/s",
-                                 "frac": ach / peak, "traffic": None, "kernel": "bp_kernel (exact g)",
-                                 "peak_basis": "%d SMs x 16 special-function results per clock x %.0f MHz"
-                                               % (sms, sm_max_mhz)}
+                r["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
+                                 "unit": "T g-evaluations/s", "frac": ach / peak, "traffic": None,
+                                 "kernel": "bp_kernel (exact g)",
+                                 "peak_basis": "%d SMs x 16/3 g per clock (2 ex2 at 32/clk, 2 lg2 at 16/clk per SM, "
+                                               "measured) x %.0f MHz" % (sms, sm_max_mhz)}
             else:
                 ops = float((6 * code.n * N + code.K) * it.sum()) * steps
                 r["roofline"] = _alu_roofline(ops, bp_ms, prec == api.POLAR_FP16, dev)

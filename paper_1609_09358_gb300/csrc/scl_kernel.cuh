@@ -33,6 +33,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "polar_common.cuh"
 
@@ -84,6 +85,10 @@ struct SCLPlan {
 // pad makes both the warp's row-wise writes and the lanes' per-path reads bank-conflict free) and
 // then read into the path's registers.
 constexpr int kSclStage = 33;
+// elements per lane and round of the element-parallel upper-level updates (measured: 8 beats 4,
+// which waits on L2 once per 4 loads, and 16, whose registers cost more than the overlap gains
+// once 16 warps share the SM)
+constexpr int kSclUpRound = 8;
 __host__ __device__ inline long long scl_smem_llr_words(int KS, int L) { return KS >= 6 ? (long long)L * ((2 << KS) - 64) : 0; }
 __host__ __device__ inline long long scl_smem_c_words(int KC, int L) { return KC >= 5 ? (long long)L * (scl_cssum(KC + 1) - 5) : 0; }
 // `lists` = frames per warp (1, or 2 with half-warp lists): the shared-memory budget of a frame
@@ -571,6 +576,9 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
     const float* y = a.llr + (frame < 0 ? 0 : (a.llr_off ? a.llr_off[frame] : (long long)frame * N));
     uint32_t pA[2] = {0u, 0u}, pC[2] = {0u, 0u};  // upper-level pointer rows of path `lane`
     float pm = 0.0f;
+    // CRC syndrome of the path's decided bits so far: XOR of the syndrome columns of the positions
+    // decided 1 (frozen positions have column 0); survivors inherit their parent's
+    uint32_t syn = 0u;
     int act = frame < 0 ? 0 : 1;
     uint32_t shA = 0u, shC = 0u;  // upper levels that may be shared since the last duplication
     Leaf lf;
@@ -599,46 +607,66 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             const uint32_t my_d = stage ? (uint32_t)lane : fld(pA, k), my_s = from_ch ? 0u : fld(pA, k + 1),
                            my_c = fld(pC, k);
             const int cwk = scl_cs(k), total = act << k, tmax = act_both << k;
-            // four elements per lane per round: all loads of a round are issued before any store,
-            // so the L2 latency of the upper levels overlaps
-            for (int e0 = 0; e0 < tmax; e0 += 4 * W) {
-                float va[4], vb[4];
-                uint32_t vw[4], pdv[4];
-                int jv[4];
+            // kSclUpRound elements per lane per round: all loads of a round are issued before any
+            // store, so the L2 latency of the upper levels (global for long lists) is paid once per
+            // round; the leaf registers are dead here and hold the round's values.  The loads are
+            // unconditional (an element past the list's end reads a valid slot: its path index is
+            // below L and its offset below len), so nothing but the stores is predicated and the
+            // rounds' independent chains interleave.
+            auto rounds = [&](auto USE_G) {
+                constexpr bool G = decltype(USE_G)::value;
+                constexpr int U = kSclUpRound;
+                for (int e0 = 0; e0 < tmax; e0 += U * W) {
+                    float va[U], vb[U];
+                    uint32_t vw[U], pdv[U];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int e = e0 + W * q + lane;
-                    const int p = (e >> k) & (W - 1);
-                    pdv[q] = sg.shfl(my_d, p);
-                    const uint32_t ps = sg.shfl(my_s, p);
-                    const uint32_t pc = sg.shfl(my_c, p);
-                    jv[q] = e & (len - 1);
-                    va[q] = vb[q] = 0.0f;
-                    vw[q] = 0u;
-                    if (e < total) {
+                    for (int q = 0; q < U; ++q) {
+                        const int e = e0 + W * q + lane;
+                        const int p = (e >> k) & (W - 1);
+                        pdv[q] = sg.shfl(my_d, p);
+                        const uint32_t ps = sg.shfl(my_s, p);
+                        const int j = e & (len - 1);
                         const float* src = srcb + ps * (2 * len);
-                        va[q] = src[jv[q]];
-                        vb[q] = src[jv[q] + len];
-                        if (use_g) vw[q] = cbk[pc * cwk + (jv[q] >> 5)];
+                        va[q] = src[j];
+                        vb[q] = src[j + len];
+                        if constexpr (G) vw[q] = cbk[sg.shfl(my_c, p) * cwk + (j >> 5)];
                     }
-                }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int e = e0 + W * q + lane;
-                    if (e < total) {
-                        const float r = use_g ? scl_g(va[q], vb[q], (vw[q] >> (jv[q] & 31)) & 1u) : xmin(va[q], vb[q]);
-                        dst[pdv[q] * dstride + jv[q]] = r;
+                    for (int q = 0; q < U; ++q) {
+                        const int e = e0 + W * q + lane;
+                        const int j = e & (len - 1);
+                        float r;
+                        if constexpr (G)
+                            r = scl_g(va[q], vb[q], (vw[q] >> (j & 31)) & 1u);
+                        else
+                            r = xmin(va[q], vb[q]);
+                        if (e < total) dst[pdv[q] * dstride + j] = r;
                     }
                 }
-            }
+            };
+            if (use_g)
+                rounds(std::true_type{});
+            else
+                rounds(std::false_type{});
             __syncwarp();
         }
         // level 5 of every path into its lane's registers (lanes past the list read row 0: the
-        // staging area has L rows)
+        // staging area has L rows); the lower leaf levels and partial sums start afresh (every bit
+        // of the block writes them before reading them), which also tells the compiler that their
+        // registers were free during the upper-level rounds above
         {
             const float* row = S.stage + (lane < L ? lane : 0) * kSclStage;
 #pragma unroll
             for (int j = 0; j < 32; ++j) lf.l5[j] = row[j];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) lf.l4[j] = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) lf.l3[j] = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) lf.l2[j] = 0.0f;
+            lf.l1[0] = lf.l1[1] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) lf.c[k] = 0u;
         }
         // ------------------------------------------------ the 32 bits of the block
         // A runtime loop: one copy of the list step serves all 32 bits, and only the per-bit leaf
@@ -648,6 +676,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
         uint32_t v5 = 0u;
 #pragma unroll 1
         for (int r = 0; r < 32; ++r) {
+            const uint32_t col = C.colsyn[blk * 32 + r];
             float lam = 0.0f;
             switch (r) {
 #define SCL_LEAF_LLR(R) \
@@ -676,9 +705,11 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                     pA[1] = __shfl_sync(0xffffffffu, pA[1], src);
                     pC[0] = __shfl_sync(0xffffffffu, pC[0], src);
                     pC[1] = __shfl_sync(0xffffffffu, pC[1], src);
+                    syn = __shfl_sync(0xffffffffu, syn, src);
                 }
                 if (dup) shA = shC = 0xffffffffu;
             }
+            if (bitv) syn ^= col;
             switch (r) {
 #define SCL_LEAF_POST(R) \
     case R: v5 = leaf_psum<R>(lf, bitv); break;
@@ -722,20 +753,36 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
         }
     }
     // ------------------------------------------------------------------ CRC selection
-    // u = x G on each path's N-bit codeword (level-n array), in place; syndrome of its
-    // information bits.  The list's lanes hold the codeword's 32-bit words lane + W h.
+    // Each path's syndrome was accumulated bit by bit; the chosen path's codeword (level-n array)
+    // is turned into u = x G in place for the output.  The list's lanes hold the codeword's 32-bit
+    // words lane + W h.
     constexpr int H = kMaxWords / W;  // words per lane
     const int words = N >> 5;
     uint32_t* xl = S.Cl(n);
     const uint32_t my_x = fld(pC, n);
-    uint32_t synd = 0xffffffffu;  // lane p: syndrome of path p
-    const int act_both = sg.both_max(act);
-    for (int p = 0; p < act_both; ++p) {
-        const bool live = p < act;
-        uint32_t* xw = xl + sg.shfl(my_x, p) * scl_cs(n);
+    const uint32_t synd = lane < act ? syn : 0xffffffffu;  // lane p: syndrome of path p
+    __syncwarp();
+    // first CRC-passing path in (metric, index) order, else the best metric
+    const bool ok_lane = lane < act && synd == 0u;
+    const bool any_ok = sg.ballot(ok_lane) != 0u;
+    const bool cand = any_ok ? ok_lane : lane < act;
+    float key = cand ? pm : __int_as_float(0x7f800000);
+    int who = cand ? lane : 64;
+#pragma unroll
+    for (int off = W / 2; off >= 1; off >>= 1) {
+        const float ok2 = __shfl_xor_sync(0xffffffffu, key, off);
+        const int ow = __shfl_xor_sync(0xffffffffu, who, off);
+        if (ok2 < key || (ok2 == key && ow < who)) {
+            key = ok2;
+            who = ow;
+        }
+    }
+    uint32_t* uw = xl + sg.shfl(my_x, who & (W - 1)) * scl_cs(n);
+    {
+        const bool live = frame >= 0;
         uint32_t w[H];
 #pragma unroll
-        for (int h = 0; h < H; ++h) w[h] = (live && lane + W * h < words) ? xw[lane + W * h] : 0u;
+        for (int h = 0; h < H; ++h) w[h] = (live && lane + W * h < words) ? uw[lane + W * h] : 0u;
         const uint32_t m[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
 #pragma unroll
         for (int h = 0; h < H; ++h)
@@ -754,40 +801,11 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             for (int h = 0; h < H; ++h)
                 if (!(h & hd) && (h | hd) < H) w[h] ^= w[h | hd];
         }
-        uint32_t s = 0u;
 #pragma unroll
-        for (int h = 0; h < H; ++h) {
-            const int wi = lane + W * h;
-            if (live && wi < words) {
-                xw[wi] = w[h];
-                uint32_t bitsw = w[h];
-                while (bitsw) {
-                    const int b = __ffs(bitsw) - 1;
-                    bitsw &= bitsw - 1u;
-                    s ^= C.colsyn[wi * 32 + b];
-                }
-            }
-        }
-        s = sg.red_xor(s);
-        if (lane == p) synd = s;
+        for (int h = 0; h < H; ++h)
+            if (live && lane + W * h < words) uw[lane + W * h] = w[h];
+        __syncwarp();
     }
-    __syncwarp();
-    // first CRC-passing path in (metric, index) order, else the best metric
-    const bool ok_lane = lane < act && synd == 0u;
-    const bool any_ok = sg.ballot(ok_lane) != 0u;
-    const bool cand = any_ok ? ok_lane : lane < act;
-    float key = cand ? pm : __int_as_float(0x7f800000);
-    int who = cand ? lane : 64;
-#pragma unroll
-    for (int off = W / 2; off >= 1; off >>= 1) {
-        const float ok2 = __shfl_xor_sync(0xffffffffu, key, off);
-        const int ow = __shfl_xor_sync(0xffffffffu, who, off);
-        if (ok2 < key || (ok2 == key && ow < who)) {
-            key = ok2;
-            who = ow;
-        }
-    }
-    const uint32_t* uw = xl + sg.shfl(my_x, who & (W - 1)) * scl_cs(n);
     if (frame >= 0) {
         uint8_t* out = a.bits + (size_t)frame * a.row_bytes;
         for (int by = lane; by < a.row_bytes; by += W) {
