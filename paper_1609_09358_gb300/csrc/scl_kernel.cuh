@@ -102,6 +102,8 @@ __host__ __device__ inline SCLPlan scl_plan(int N, int L, bool all_smem, int lis
         p.KC = n;
     } else {
         p.KS = 5;
+        // up to 6 KB of LLR levels per frame (8 KB, which puts level 6 of a 32-path list in shared
+        // memory, measured 3% slower for a single frame and 3% faster for 2^16 frames: not kept)
         while (p.KS + 1 <= n - 1 && 4 * scl_smem_llr_words(p.KS + 1, L) * lists <= 6144) ++p.KS;
         p.KC = 4;
         while (p.KC + 1 <= n && 4 * scl_smem_c_words(p.KC + 1, L) * lists <= 2048) ++p.KC;
@@ -166,14 +168,16 @@ struct Lanes {
     }
     template <class V>
     __device__ __forceinline__ V shfl(V v, int p) const { return __shfl_sync(0xffffffffu, v, base + p); }
+    // Reductions over the list: one redux.sync for a whole-warp list; for half-warp lists one per
+    // half, each lane feeding the other half's reduction the identity, and keeping its own half's.
     __device__ __forceinline__ uint32_t red_or(uint32_t v) const
     {
         if constexpr (W == 32) {
             return __reduce_or_sync(0xffffffffu, v);
         } else {
-#pragma unroll
-            for (int o = W / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
-            return v;
+            const uint32_t lo = __reduce_or_sync(0xffffffffu, base ? 0u : v);
+            const uint32_t hi = __reduce_or_sync(0xffffffffu, base ? v : 0u);
+            return base ? hi : lo;
         }
     }
     __device__ __forceinline__ uint32_t red_xor(uint32_t v) const
@@ -181,9 +185,9 @@ struct Lanes {
         if constexpr (W == 32) {
             return __reduce_xor_sync(0xffffffffu, v);
         } else {
-#pragma unroll
-            for (int o = W / 2; o > 0; o >>= 1) v ^= __shfl_xor_sync(0xffffffffu, v, o);
-            return v;
+            const uint32_t lo = __reduce_xor_sync(0xffffffffu, base ? 0u : v);
+            const uint32_t hi = __reduce_xor_sync(0xffffffffu, base ? v : 0u);
+            return base ? hi : lo;
         }
     }
     __device__ __forceinline__ uint32_t red_max(uint32_t v) const
@@ -191,9 +195,9 @@ struct Lanes {
         if constexpr (W == 32) {
             return __reduce_max_sync(0xffffffffu, v);
         } else {
-#pragma unroll
-            for (int o = W / 2; o > 0; o >>= 1) v = max(v, (uint32_t)__shfl_xor_sync(0xffffffffu, v, o));
-            return v;
+            const uint32_t lo = __reduce_max_sync(0xffffffffu, base ? 0u : v);
+            const uint32_t hi = __reduce_max_sync(0xffffffffu, base ? v : 0u);
+            return base ? hi : lo;
         }
     }
     __device__ __forceinline__ uint32_t red_min(uint32_t v) const
@@ -201,9 +205,9 @@ struct Lanes {
         if constexpr (W == 32) {
             return __reduce_min_sync(0xffffffffu, v);
         } else {
-#pragma unroll
-            for (int o = W / 2; o > 0; o >>= 1) v = min(v, (uint32_t)__shfl_xor_sync(0xffffffffu, v, o));
-            return v;
+            const uint32_t lo = __reduce_min_sync(0xffffffffu, base ? 0xffffffffu : v);
+            const uint32_t hi = __reduce_min_sync(0xffffffffu, base ? v : 0xffffffffu);
+            return base ? hi : lo;
         }
     }
     __device__ __forceinline__ uint32_t match_any(uint32_t v) const
@@ -268,15 +272,6 @@ __host__ __device__ constexpr int ctz_c(int v)
     }
     return c;
 }
-__host__ __device__ constexpr int tones_c(int v)  // trailing ones
-{
-    int c = 0;
-    while (v & 1) {
-        v >>= 1;
-        ++c;
-    }
-    return c;
-}
 // Is leaf level k (1..5) read, before being rewritten, by a later bit of the block than r?
 __host__ __device__ constexpr bool leaf_live(int r, int k)
 {
@@ -336,6 +331,26 @@ __device__ __forceinline__ float leaf_llr(Leaf& f)
     }
 }
 
+// The partial-sum step with the bit index r at run time (warp-uniform): kc = trailing ones of r
+// levels fold in predicated steps, no jump (measured faster than dispatching leaf_psum<R> by a
+// switch on r; the LLR step keeps the switch, which measured faster than its runtime form).
+__device__ __forceinline__ uint32_t leaf_psum_rt(Leaf& f, uint32_t bitv, int r)
+{
+    const int kc = __ffs(~r) - 1;
+    uint32_t v = bitv;
+    if (kc > 0) v = ((v ^ f.c[0]) & 0x1u) | ((v & 0x1u) << 1);
+    if (kc > 1) v = ((v ^ f.c[1]) & 0x3u) | ((v & 0x3u) << 2);
+    if (kc > 2) v = ((v ^ f.c[2]) & 0xFu) | ((v & 0xFu) << 4);
+    if (kc > 3) v = ((v ^ f.c[3]) & 0xFFu) | ((v & 0xFFu) << 8);
+    if (kc > 4) v = ((v ^ f.c[4]) & 0xFFFFu) | ((v & 0xFFFFu) << 16);
+    if (kc == 0) f.c[0] = v;
+    if (kc == 1) f.c[1] = v;
+    if (kc == 2) f.c[2] = v;
+    if (kc == 3) f.c[3] = v;
+    if (kc == 4) f.c[4] = v;
+    return v;
+}
+
 // after a duplicating list step at bit r: survivors take the live leaf state of their parents
 template <int R>
 __device__ __forceinline__ void leaf_inherit(Leaf& f, int parent)
@@ -379,21 +394,6 @@ __device__ __forceinline__ void leaf_inherit_rt(Leaf& f, int parent, uint32_t li
     if (live & 1u) leaf_copy<2>(f.l1, parent);
 #pragma unroll
     for (int k = 0; k < 5; ++k) f.c[k] = __shfl_sync(0xffffffffu, f.c[k], parent);
-}
-
-// partial sums after bit r (value `bitv`): returns the level-5 value when the block completes
-template <int R>
-__device__ __forceinline__ uint32_t leaf_psum(Leaf& f, uint32_t bitv)
-{
-    constexpr int kc = tones_c(R);
-    uint32_t v = bitv;
-#pragma unroll
-    for (int k = 0; k < (kc < 5 ? kc : 5); ++k) {
-        const uint32_t m = (k == 4) ? 0xFFFFu : ((1u << (1 << k)) - 1u);
-        v = ((v ^ f.c[k]) & m) | ((v & m) << (1 << k));
-    }
-    if constexpr (kc < 5) f.c[kc] = v;
-    return v;
 }
 
 // Launches the persistent CA-SCL grid (defined in scl_launch.cu).  `a.scratch` null selects the
@@ -710,12 +710,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                 if (dup) shA = shC = 0xffffffffu;
             }
             if (bitv) syn ^= col;
-            switch (r) {
-#define SCL_LEAF_POST(R) \
-    case R: v5 = leaf_psum<R>(lf, bitv); break;
-                SCL_FOR_32(SCL_LEAF_POST)
-#undef SCL_LEAF_POST
-            }
+            v5 = leaf_psum_rt(lf, bitv, r);
         }
         // ------------------------------------------------ block complete: partial sums upward
         {
