@@ -10,6 +10,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "bp_launch.cuh"
@@ -363,13 +364,15 @@ static int launch_bp(const DevCode* dcode, const polar_code* code, const float* 
                                                : bp_kernel_info_fp32(n, w != nullptr);
     if (!k.fn) return fail(POLAR_ERR_ARG, "no BP kernel for N = %d with these options", code->N);
     if (k.smem > 48 * 1024) {
-        // above the default dynamic shared-memory limit (N = 4096); set once per kernel
+        // above the default dynamic shared-memory limit (N = 4096); set once per kernel and device
         static std::mutex m;
-        static std::vector<const void*> done;
+        static std::vector<std::pair<int, const void*>> done;
+        int dev = 0;
+        POLAR_CUDA(cudaGetDevice(&dev));
         std::lock_guard<std::mutex> lock(m);
-        if (std::find(done.begin(), done.end(), k.fn) == done.end()) {
+        if (std::find(done.begin(), done.end(), std::make_pair(dev, k.fn)) == done.end()) {
             POLAR_CUDA(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
-            done.push_back(k.fn);
+            done.push_back(std::make_pair(dev, k.fn));
         }
     }
     const int fpt = precision == POLAR_FP16 ? 2 : 1;
