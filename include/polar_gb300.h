@@ -211,7 +211,7 @@ int wms_backward(const polar_code* code, const float* llr, int32_t B, int32_t T,
  * POLAR_MAX_MIX_CODES codes of different lengths and rates in one batch.  Frames are bucketed by
  * code on the device, then one persistent BP launch decodes all of them (a CTA works on one code
  * at a time and moves to the next when that code's queue is empty) and one CA-SCL launch decodes
- * every frame whose CRC failed, each with its own code.  Nothing waits for the host, so the call
+ * every frame whose CRC failed, each with its own code (failures sorted by code first).  Nothing waits for the host, so the call
  * can be captured in a CUDA graph once each code has been used (code tables uploaded) and
  * polar_mixed_autotune has run.  Results equal hybrid_decode of each frame with its own code.
  *   codes: host array of ncodes code descriptions.  code_of: device int32 [B], code of each frame

@@ -44,6 +44,9 @@ __host__ __device__ constexpr int mix_cta_words()
 const void* bp_mixed_fn(int precision, bool packed_syndrome);
 cudaError_t mix_bucketing(const int* code_of, int B, int ncodes, int* counts, int* start, int* cursor, int* order,
                           cudaStream_t st);
+// the first *count entries of list (frame indices, *count <= cap) sorted by code into sorted
+cudaError_t mix_sort_list(const int* list, const int* count, int cap, const int* code_of, int ncodes, int* counts,
+                          int* start, int* cursor, int* sorted, cudaStream_t st);
 
 inline size_t mix_smem_bytes(int variant)
 {
@@ -124,6 +127,27 @@ __global__ void mix_scatter_kernel(const int* __restrict__ code_of, int B, int n
     if (b < B) {
         const int c = code_of[b];
         if (c >= 0 && c < ncodes) order[atomicAdd(&cursor[c], 1)] = b;
+    }
+}
+
+// The same three steps over the entries of a list (the frames CA-SCL decodes).
+__global__ void mix_count_list_kernel(const int* __restrict__ list, const int* count, const int* __restrict__ code_of,
+                                      int ncodes, int* counts)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < *count) {
+        const int c = code_of[list[i]];
+        if (c >= 0 && c < ncodes) atomicAdd(&counts[c], 1);
+    }
+}
+__global__ void mix_scatter_list_kernel(const int* __restrict__ list, const int* count, const int* __restrict__ code_of,
+                                        int ncodes, int* cursor, int* sorted)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < *count) {
+        const int f = list[i];
+        const int c = code_of[f];
+        if (c >= 0 && c < ncodes) sorted[atomicAdd(&cursor[c], 1)] = f;
     }
 }
 

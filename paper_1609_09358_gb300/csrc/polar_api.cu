@@ -968,8 +968,10 @@ int mix_check(const polar_code* codes, int ncodes, int B, int L, int row_stride,
             return fail(POLAR_ERR_ARG, "mixed batches: N = %d > %d", codes[c].N, POLAR_MAX_N_MIXED);
         mr = std::max(mr, (codes[c].K - codes[c].crc_len + 7) / 8);
         if (L > 0) {
-            const SCLPlan p = scl_plan(codes[c].N, L, false);
-            ww = std::max(ww, p.warp_words);
+            // per-list words (+ the warp's 16 scratch words) and global slot of the CA-SCL launch's
+            // list width (two lists per warp for L <= 8)
+            const SCLPlan p = scl_plan(codes[c].N, L, false, scl_two_lists(L, false) ? 2 : 1);
+            ww = std::max(ww, p.list_words + 16);
             sw = std::max(sw, p.slot_words);
         }
     }
@@ -1089,6 +1091,12 @@ int hybrid_decode_mixed(const polar_code* codes, int32_t ncodes, const int32_t* 
                      row_stride, status, iters, base, ml, st)))
         return rc;
     int* hdr = reinterpret_cast<int*>(base);
+    // the CRC failures sorted by code (into the BP bucketing's order array, free after BP), so that
+    // the two half-warp lists of a CA-SCL warp mostly decode frames of one code
+    int* sorted = reinterpret_cast<int*>(base + ml.order);
+    POLAR_CUDA(mix_sort_list(reinterpret_cast<int*>(base + ml.list), hdr + 1, B, code_of, ncodes,
+                             reinterpret_cast<int*>(base + ml.counts), reinterpret_cast<int*>(base + ml.start),
+                             reinterpret_cast<int*>(base + ml.cursor), sorted, st));
     SCLArgs a{};
     a.llr = llr;
     a.B = B;
@@ -1096,7 +1104,7 @@ int hybrid_decode_mixed(const polar_code* codes, int32_t ncodes, const int32_t* 
     a.bits = bits;
     a.status = status;
     a.code = dcodes[0];
-    a.list = reinterpret_cast<int*>(base + ml.list);
+    a.list = sorted;
     a.count = hdr + 1;
     a.next = hdr + 2;
     a.scratch = reinterpret_cast<float*>(base + ml.scratch);

@@ -128,7 +128,7 @@ inline int scl_sm_count()
 }
 // List width of a CA-SCL launch: two frames per warp (half-warp lists) for L <= 8 in the global
 // layout with a single code.
-inline bool scl_two_lists(int L, bool all_smem, bool one_code) { return L <= 8 && !all_smem && one_code; }
+inline bool scl_two_lists(int L, bool all_smem) { return L <= 8 && !all_smem; }
 // global workspace of the SCL list arrays (one slot per resident list: up to kSclWarpsPerSM lists
 // per SM)
 inline size_t scl_scratch_bytes(int N, int L)
@@ -818,17 +818,21 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
     __syncwarp();
 }
 
-// Decode `frame` (frame < 0: nothing, on this lane's list) by the calling warp: plan of its code,
-// the list's shared words `ws` and global slot `slot` (null: every level in shared memory).
+// Decode `frame` (frame < 0: nothing, on this lane's list) by the calling warp with code `code_id`
+// of a mixed batch (-1: the batch's single code): plan of the code, the list's shared words `ws`
+// and global slot `slot` (null: every level in shared memory).  A list without a frame still walks
+// the code's structure with no path, so both lists of a warp must be given the same code.
 template <bool TWO, int W>
-__device__ __forceinline__ void scl_warp_frame(const SCLArgs& a, int frame, uint32_t* ws, float* slot, uint8_t* selc)
+__device__ __forceinline__ void scl_warp_frame(const SCLArgs& a, int frame, int code_id, uint32_t* ws, float* slot,
+                                               uint8_t* selc)
 {
+    constexpr int LISTS = 32 / W;
     const int L = a.L;
-    const DevCode& C = (a.code_of && frame >= 0) ? *a.codes[a.code_of[frame]] : *a.code;
+    const DevCode& C = code_id >= 0 ? *a.codes[code_id] : *a.code;
     SCLWarp S;
     S.L = L;
     if (a.code_of) {
-        const SCLPlan p = scl_plan(C.N, L, slot == nullptr);
+        const SCLPlan p = scl_plan(C.N, L, slot == nullptr, LISTS);
         S.KS = p.KS;
         S.KC = p.KC;
     } else {
@@ -843,7 +847,9 @@ __device__ __forceinline__ void scl_warp_frame(const SCLArgs& a, int frame, uint
     scl_decode_frame<TWO, W>(a, C, frame, S, selc);
 }
 
-// W = 32: one frame per warp; W = 16: two (one per half-warp list), claimed together.
+// W = 32: one frame per warp; W = 16: two (one per half-warp list), claimed together.  In a mixed
+// batch (frames sorted by code) the two frames of a pair normally share their code; a pair whose
+// codes differ is decoded one list after the other.
 template <bool TWO, int W>
 __global__ void __launch_bounds__(kSclWarpsPerCTA * 32) scl_kernel(const SCLArgs a)
 {
@@ -865,7 +871,22 @@ __global__ void __launch_bounds__(kSclWarpsPerCTA * 32) scl_kernel(const SCLArgs
         if (idx >= count) break;  // uniform over the warp
         const int k = idx + li;
         const int frame = k < count ? (a.list ? a.list[k] : k) : -1;
-        scl_warp_frame<TWO, W>(a, frame, ws, slot, selc);
+        if (!a.code_of) {
+            scl_warp_frame<TWO, W>(a, frame, -1, ws, slot, selc);
+            continue;
+        }
+        const int cf = frame >= 0 ? a.code_of[frame] : -1;
+        if constexpr (LISTS == 2) {
+            const int c0 = __shfl_sync(0xffffffffu, cf, 0), c1 = __shfl_sync(0xffffffffu, cf, 16);
+            if (c0 >= 0 && c1 >= 0 && c0 != c1) {
+                scl_warp_frame<TWO, W>(a, li == 0 ? frame : -1, c0, ws, slot, selc);
+                scl_warp_frame<TWO, W>(a, li == 1 ? frame : -1, c1, ws, slot, selc);
+            } else {
+                scl_warp_frame<TWO, W>(a, frame, c0 >= 0 ? c0 : c1, ws, slot, selc);
+            }
+        } else {
+            scl_warp_frame<TWO, W>(a, frame, cf, ws, slot, selc);
+        }
     }
 }
 
@@ -874,7 +895,7 @@ __global__ void __launch_bounds__(kSclWarpsPerCTA * 32) scl_kernel(const SCLArgs
 cudaError_t scl_launch(SCLArgs a, int N, int L, cudaStream_t st, int warp_words_max, long long slot_words_max)
 {
     const bool all_smem = a.scratch == nullptr;
-    const int lists = scl_two_lists(L, all_smem, a.code_of == nullptr) ? 2 : 1;
+    const int lists = scl_two_lists(L, all_smem) ? 2 : 1;
     const SCLPlan p = scl_plan(N, L, all_smem, lists);
     a.KS = p.KS;
     a.KC = p.KC;
