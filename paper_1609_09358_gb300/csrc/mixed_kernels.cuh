@@ -44,9 +44,13 @@ __host__ __device__ constexpr int mix_cta_words()
 const void* bp_mixed_fn(int precision, bool packed_syndrome);
 cudaError_t mix_bucketing(const int* code_of, int B, int ncodes, int* counts, int* start, int* cursor, int* order,
                           cudaStream_t st);
-// the first *count entries of list (frame indices, *count <= cap) sorted by code into sorted
-cudaError_t mix_sort_list(const int* list, const int* count, int cap, const int* code_of, int ncodes, int* counts,
-                          int* start, int* cursor, int* sorted, cudaStream_t st);
+// the first *count entries of list (frame indices, *count <= cap) sorted into `sorted` by the rank
+// of their code (rank.r[code]: a permutation of 0 .. ncodes-1)
+struct MixRank {
+    int r[kMixMaxCodes];
+};
+cudaError_t mix_sort_list(const int* list, const int* count, int cap, const int* code_of, int ncodes, MixRank rank,
+                          int* counts, int* start, int* cursor, int* sorted, cudaStream_t st);
 
 inline size_t mix_smem_bytes(int variant)
 {
@@ -132,22 +136,22 @@ __global__ void mix_scatter_kernel(const int* __restrict__ code_of, int B, int n
 
 // The same three steps over the entries of a list (the frames CA-SCL decodes).
 __global__ void mix_count_list_kernel(const int* __restrict__ list, const int* count, const int* __restrict__ code_of,
-                                      int ncodes, int* counts)
+                                      int ncodes, MixRank rank, int* counts)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < *count) {
         const int c = code_of[list[i]];
-        if (c >= 0 && c < ncodes) atomicAdd(&counts[c], 1);
+        if (c >= 0 && c < ncodes) atomicAdd(&counts[rank.r[c]], 1);
     }
 }
 __global__ void mix_scatter_list_kernel(const int* __restrict__ list, const int* count, const int* __restrict__ code_of,
-                                        int ncodes, int* cursor, int* sorted)
+                                        int ncodes, MixRank rank, int* cursor, int* sorted)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < *count) {
         const int f = list[i];
         const int c = code_of[f];
-        if (c >= 0 && c < ncodes) sorted[atomicAdd(&cursor[c], 1)] = f;
+        if (c >= 0 && c < ncodes) sorted[atomicAdd(&cursor[rank.r[c]], 1)] = f;
     }
 }
 

@@ -11,16 +11,16 @@ const void* bp_mixed_fn(int precision, bool packed_syndrome)
     return packed_syndrome ? (const void*)bp_mixed_kernel<__half2, true> : (const void*)bp_mixed_kernel<__half2, false>;
 }
 
-cudaError_t mix_sort_list(const int* list, const int* count, int cap, const int* code_of, int ncodes, int* counts,
-                          int* start, int* cursor, int* sorted, cudaStream_t st)
+cudaError_t mix_sort_list(const int* list, const int* count, int cap, const int* code_of, int ncodes, MixRank rank,
+                          int* counts, int* start, int* cursor, int* sorted, cudaStream_t st)
 {
     if (cap <= 0) return cudaSuccess;
     const int tb = 256, nb = (cap + tb - 1) / tb;
     cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)ncodes, st);
     if (e != cudaSuccess) return e;
-    mix_count_list_kernel<<<nb, tb, 0, st>>>(list, count, code_of, ncodes, counts);
+    mix_count_list_kernel<<<nb, tb, 0, st>>>(list, count, code_of, ncodes, rank, counts);
     mix_scan_kernel<<<1, 1, 0, st>>>(counts, ncodes, start, cursor);
-    mix_scatter_list_kernel<<<nb, tb, 0, st>>>(list, count, code_of, ncodes, cursor, sorted);
+    mix_scatter_list_kernel<<<nb, tb, 0, st>>>(list, count, code_of, ncodes, rank, cursor, sorted);
     return cudaGetLastError();
 }
 

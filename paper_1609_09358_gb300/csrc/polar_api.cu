@@ -1091,10 +1091,18 @@ int hybrid_decode_mixed(const polar_code* codes, int32_t ncodes, const int32_t* 
                      row_stride, status, iters, base, ml, st)))
         return rc;
     int* hdr = reinterpret_cast<int*>(base);
-    // the CRC failures sorted by code (into the BP bucketing's order array, free after BP), so that
-    // the two half-warp lists of a CA-SCL warp mostly decode frames of one code
+    // The CRC failures sorted by code (into the BP bucketing's order array, free after BP), so that
+    // the two half-warp lists of a CA-SCL warp mostly decode frames of one code; longest codes
+    // first, so that the frames with the longest decoding latency do not start last.
+    MixRank rank{};
+    {
+        int idx[POLAR_MAX_MIX_CODES];
+        for (int c = 0; c < ncodes; ++c) idx[c] = c;
+        std::stable_sort(idx, idx + ncodes, [&](int x, int y) { return codes[x].N > codes[y].N; });
+        for (int r = 0; r < ncodes; ++r) rank.r[idx[r]] = r;
+    }
     int* sorted = reinterpret_cast<int*>(base + ml.order);
-    POLAR_CUDA(mix_sort_list(reinterpret_cast<int*>(base + ml.list), hdr + 1, B, code_of, ncodes,
+    POLAR_CUDA(mix_sort_list(reinterpret_cast<int*>(base + ml.list), hdr + 1, B, code_of, ncodes, rank,
                              reinterpret_cast<int*>(base + ml.counts), reinterpret_cast<int*>(base + ml.start),
                              reinterpret_cast<int*>(base + ml.cursor), sorted, st));
     SCLArgs a{};
