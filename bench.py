@@ -197,8 +197,9 @@ def run_reference(a, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * secs / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(a).replace("%d frames per GPU per step" % a.frames,
-                                                            "%d frames per step (CPU sample)" % per_step)},
+            "config": {"workload": workload_name(a), "ebn0_db": a.ebn0, "N": N, "K": K, "crc": "CRC-16 0x1021",
+                       "i_max": IMAX, "L": LIST, "llr_max": LLR_MAX,
+                       "sample": "%d seeded frames of this workload per step, timed on the host cores" % per_step},
             "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
                              "sample": "%d seeded frames per step of the same workload, C oracle with OpenMP" % per_step},
             "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
