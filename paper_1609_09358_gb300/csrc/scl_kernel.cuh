@@ -565,11 +565,16 @@ __device__ __forceinline__ int scl_list_step_half(float lam, float& pm, int& act
 
 // Decode one frame per list: the warp's frame (W = 32), or each half-warp's frame (W = 16; a
 // half without a frame passes frame < 0 and decodes nothing).  TWO: L = 32, two candidates per
-// lane.
-template <bool TWO, int W>
-__device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, const SCLWarp& S, uint8_t* selc)
+// lane.  MW: every warp of the CTA calls with the same frame; warp 0 holds the list and runs the
+// bit loop, and all warps share the element-parallel upper-level updates (their path pointers
+// and path count passed through `ptab`, 104 shared words), with CTA barriers around each level.
+template <bool TWO, int W, bool MW = false>
+__device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, const SCLWarp& S, uint8_t* selc,
+                                 uint32_t* ptab = nullptr)
 {
     static_assert(W == 32 || !TWO, "half-warp lists hold at most 8 paths");
+    static_assert(!MW || W == 32, "the multi-warp form takes whole-warp lists");
+    const bool lead = !MW || threadIdx.x < 32;
     const Lanes<W> sg;
     const int lane = sg.pl;  // path of this lane within its list
     const int N = C.N, n = C.n, L = a.L;
@@ -593,7 +598,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
         for (int k = top; k >= 5; --k) {
             // level 5 goes to the staging rows (indexed by path), levels >= 6 to their arrays
             const bool stage = k == 5;
-            if (!stage && __any_sync(0xffffffffu, (shA >> k) & 1u)) {
+            if (lead && !stage && __any_sync(0xffffffffu, (shA >> k) & 1u)) {
                 scl_own<W>(pA, k, act, L);
                 shA &= ~(1u << k);
             }
@@ -606,7 +611,20 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             const uint32_t* cbk = S.Cl(k);
             const uint32_t my_d = stage ? (uint32_t)lane : fld(pA, k), my_s = from_ch ? 0u : fld(pA, k + 1),
                            my_c = fld(pC, k);
-            const int cwk = scl_cs(k), total = act << k, tmax = act_both << k;
+            int nact = act, nact_both = act_both;
+            if constexpr (MW) {
+                if (lead) {
+                    ptab[lane] = my_d;
+                    ptab[32 + lane] = my_s;
+                    ptab[64 + lane] = my_c;
+                    if (lane == 0) ptab[96] = (uint32_t)act;
+                }
+                __syncthreads();
+                nact = nact_both = (int)ptab[96];
+            }
+            const int cwk = scl_cs(k), total = nact << k, tmax = nact_both << k;
+            // element stride of a round: the list's lanes, or every thread of the CTA
+            const int TW = MW ? (int)blockDim.x : W, tix = MW ? (int)threadIdx.x : lane;
             // kSclUpRound elements per lane per round: all loads of a round are issued before any
             // store, so the L2 latency of the upper levels (global for long lists) is paid once per
             // round; the leaf registers are dead here and hold the round's values.  The loads are
@@ -616,24 +634,24 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             auto rounds = [&](auto USE_G) {
                 constexpr bool G = decltype(USE_G)::value;
                 constexpr int U = kSclUpRound;
-                for (int e0 = 0; e0 < tmax; e0 += U * W) {
+                for (int e0 = 0; e0 < tmax; e0 += U * TW) {
                     float va[U], vb[U];
                     uint32_t vw[U], pdv[U];
 #pragma unroll
                     for (int q = 0; q < U; ++q) {
-                        const int e = e0 + W * q + lane;
+                        const int e = e0 + TW * q + tix;
                         const int p = (e >> k) & (W - 1);
-                        pdv[q] = sg.shfl(my_d, p);
-                        const uint32_t ps = sg.shfl(my_s, p);
+                        pdv[q] = MW ? ptab[p] : sg.shfl(my_d, p);
+                        const uint32_t ps = MW ? ptab[32 + p] : sg.shfl(my_s, p);
                         const int j = e & (len - 1);
                         const float* src = srcb + ps * (2 * len);
                         va[q] = src[j];
                         vb[q] = src[j + len];
-                        if constexpr (G) vw[q] = cbk[sg.shfl(my_c, p) * cwk + (j >> 5)];
+                        if constexpr (G) vw[q] = cbk[(MW ? ptab[64 + p] : sg.shfl(my_c, p)) * cwk + (j >> 5)];
                     }
 #pragma unroll
                     for (int q = 0; q < U; ++q) {
-                        const int e = e0 + W * q + lane;
+                        const int e = e0 + TW * q + tix;
                         const int j = e & (len - 1);
                         float r;
                         if constexpr (G)
@@ -648,8 +666,12 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                 rounds(std::true_type{});
             else
                 rounds(std::false_type{});
-            __syncwarp();
+            if constexpr (MW)
+                __syncthreads();
+            else
+                __syncwarp();
         }
+        if (!lead) continue;  // the helper warps only share the upper levels
         // level 5 of every path into its lane's registers (lanes past the list read row 0: the
         // staging area has L rows); the lower leaf levels and partial sums start afresh (every bit
         // of the block writes them before reading them), which also tells the compiler that their
@@ -747,6 +769,7 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             }
         }
     }
+    if (!lead) return;
     // ------------------------------------------------------------------ CRC selection
     // Each path's syndrome was accumulated bit by bit; the chosen path's codeword (level-n array)
     // is turned into u = x G in place for the output.  The list's lanes hold the codeword's 32-bit
@@ -864,6 +887,38 @@ __global__ void __launch_bounds__(kSclWarpsPerCTA * 32) scl_kernel(const SCLArgs
         ? a.scratch + (((size_t)blockIdx.x * (blockDim.x >> 5) + wid) * LISTS + li) * (size_t)a.slot_words
         : nullptr;
     const int count = a.count ? *a.count : a.B;
+    if constexpr (W == 32) {
+        // Few frames (at most one per CTA, single code): each CTA takes one frame at a time and
+        // all its warps share the frame's upper-level updates (the words of warp 1, unused here,
+        // hold the shared path pointers), which shortens the frame's decoding latency.
+        if (!a.code_of && count <= (int)gridDim.x && blockDim.x >= 64) {
+            uint32_t* ptab = smem + a.warp_words;
+            for (;;) {
+                if (threadIdx.x == 0) ptab[100] = (uint32_t)atomicAdd(a.next, 1);
+                __syncthreads();
+                const int idx = (int)ptab[100];
+                __syncthreads();
+                if (idx >= count) break;  // uniform over the CTA
+                const int frame = a.list ? a.list[idx] : idx;
+                SCLWarp S;
+                S.L = a.L;
+                S.KS = a.KS;
+                S.KC = a.KC;
+                uint32_t* ws0 = smem;  // warp 0's list words
+                S.sC = ws0;
+                S.sA = reinterpret_cast<float*>(ws0 + scl_smem_c_words(S.KC, a.L));
+                S.stage = S.sA + scl_smem_llr_words(S.KS, a.L);
+                float* slot0 = a.scratch ? a.scratch + ((size_t)blockIdx.x * (blockDim.x >> 5) * LISTS) * (size_t)a.slot_words
+                                         : nullptr;
+                S.gA = slot0;
+                S.gC = slot0 ? reinterpret_cast<uint32_t*>(slot0 + (size_t)a.L * (a.code->N - (2 << S.KS))) : nullptr;
+                scl_decode_frame<TWO, W, true>(a, *a.code, frame, S, reinterpret_cast<uint8_t*>(smem + a.warp_words - 16),
+                                               ptab);
+                __syncthreads();
+            }
+            return;
+        }
+    }
     for (;;) {
         int idx = 0;
         if (lane == 0) idx = atomicAdd(a.next, LISTS);
@@ -918,7 +973,12 @@ cudaError_t scl_launch(SCLArgs a, int N, int L, cudaStream_t st, int warp_words_
     const int sms = scl_sm_count();
     long long grid = (long long)sms * per_sm;
     if (!all_smem) grid = std::min<long long>(grid, (long long)sms * kSclWarpsPerSM / (W * lists));
-    if (!a.list) grid = std::min<long long>(grid, (a.B + W * lists - 1) / (W * lists));
+    if (!a.list) {
+        // known work: whole-warp lists with at most one frame per CTA of the full grid get a CTA
+        // per frame (its warps then share each frame's upper levels), otherwise no idle CTAs
+        const long long need = (a.B + W * lists - 1) / (W * lists);
+        grid = (lists == 1 && W > 1 && !a.code_of && a.B <= grid) ? std::max(a.B, 1) : std::min(grid, need);
+    }
     if (grid < 1) grid = 1;
     if (lists == 2)
         scl_kernel<false, 16><<<(unsigned)grid, W * 32, smem, st>>>(a);

@@ -240,6 +240,19 @@ def test_scl_global_scratch_path():
     assert np.array_equal(bits, oracle.payload_of(ref["u_hat"], ocode))
 
 
+@pytest.mark.parametrize("L,B", [(32, 2500), (16, 2500), (32, 40), (16, 7)])
+def test_scl_few_and_many_frames(L, B):
+    """With at most one frame per CTA of the persistent grid, a CTA's warps share each frame's
+    upper-level updates; with more frames every warp decodes its own.  Both forms are bit-exact
+    (2 500 frames exceed every grid this launch can have; 40 and 7 do not)."""
+    ocode = fr.oracle_code(128, 64, 8)
+    _, llr = fr.frames(ocode, 0.5, B, seed=91 + B + L)
+    ref = oracle.scl_decode(llr, ocode, L, "f32")
+    bits, status = run_scl(ocode, llr, L)
+    assert np.array_equal(status, ref["status"])
+    assert np.array_equal(bits, oracle.payload_of(ref["u_hat"], ocode))
+
+
 def run_hybrid(ocode, llr, imax, L, llr_max=20.0, precision=api.POLAR_FP32):
     code = fr.api_code(ocode)
     B = llr.shape[0]
