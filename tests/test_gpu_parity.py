@@ -384,3 +384,42 @@ def test_hybrid_multi_chunk_every_frame():
     assert np.array_equal(iters, ref["iters"])
     assert np.array_equal(status, ref["status"])
     assert np.array_equal(bits, oracle.payload_of(ref["u_hat"], ocode))
+
+
+def test_stress_batch_full_size_sampled():
+    """The fallback-heavy stress workload's batch as the benchmark launches it (N = 2048, K = 1024,
+    CRC-24, 1.5 dB, 2^16 frames, learned half2 BP with the trained 20-iteration scales, then CA-SCL
+    L = 32): the status of every frame is valid and the decoded bits, status and iterations of a
+    sample (random frames and CA-SCL frames) equal the oracle's half-precision weighted BP followed
+    by its CA-SCL, frame by frame."""
+    import os
+    from paper_1609_09358_gb300 import wms
+    wfile = os.path.join(os.path.dirname(api.__file__), "weights", "wms_n2048_k1024_t20.pt")
+    if not os.path.exists(wfile):
+        pytest.skip("no trained weights for N = 2048")
+    w, code, T, _ = wms.load(wfile, device="cuda")
+    ocode = fr.oracle_code(2048, 1024, 24)
+    assert np.array_equal(ocode.frozen, code.frozen)
+    B = 1 << 16
+    _, llr = fr.frames_large(ocode, 1.5, B, seed=1609093577)
+    pw = api.PreparedScales(code, w, api.POLAR_FP16)
+    dec = api.Decoder(code, B, L=32)
+    dec.hybrid(torch.from_numpy(llr).cuda(), T, 32.0, api.POLAR_FP16, pw)
+    torch.cuda.synchronize()
+    status = dec.status.cpu().numpy()
+    iters = dec.iters.cpu().numpy().astype(np.int32)
+    assert set(np.unique(status)) <= {1, 2, 3}
+    rng = np.random.default_rng(5)
+    fb = np.nonzero(status != oracle.BP_OK)[0]
+    ok = np.nonzero(status == oracle.BP_OK)[0]
+    sample = np.unique(np.concatenate([rng.choice(B, 12, replace=False), fb[:6], ok[:6]]))
+    rows = llr[sample]
+    bp = oracle.bp_decode(rows, ocode, T, 32.0, "f16", w=w.cpu().numpy(), want_llr=False)
+    u, st = bp["u_hat"].copy(), bp["status"].copy()
+    failed = st != oracle.BP_OK
+    if failed.any():
+        scl = oracle.scl_decode(rows[failed], ocode, 32, "f32")
+        u[failed], st[failed] = scl["u_hat"], scl["status"]
+    assert np.array_equal(iters[sample], bp["iters"])
+    assert np.array_equal(status[sample], st)
+    assert np.array_equal(api.unpack_bits(dec.bits.cpu().numpy()[sample], ocode.P), oracle.payload_of(u, ocode))

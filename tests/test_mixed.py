@@ -105,3 +105,35 @@ def test_mixed_batch_cuda_graph_replay():
     ref = reference(ocodes, code_of, off, llr, 40, 8, "f32")
     check(ocodes, code_of, dec.bits.cpu().numpy(), dec.status.cpu().numpy(),
           dec.iters.cpu().numpy().astype(np.int32), ref)
+
+
+def test_mixed_full_size_sampled():
+    """The mixed workload at its full size and in the launch configuration the benchmark times
+    (2^16 frames of the 15 codes at 2.0 dB, i_max = 200, L = 8, half2 BP, autotuned plans, CUDA
+    graph replay): a random sample of frames and the first CA-SCL frames of every code are
+    decoded one by one by the oracle and compared."""
+    build.build()
+    B = 1 << 16
+    ocodes, code_of, off, llr = mixed_batch(B, 2.0, 2024)
+    codes = [fr.api_code(oc) for oc in ocodes]
+    dec = api.MixedDecoder(codes, B, L=8)
+    args = (torch.from_numpy(code_of).cuda(), torch.from_numpy(off).cuda(), torch.from_numpy(llr).cuda())
+    dec.autotune(*args, 200, 32.0, api.POLAR_FP16)
+    dec.capture(*args, 200, 32.0, api.POLAR_FP16)
+    dec.replay()
+    torch.cuda.synchronize()
+    dstat = dec.status.cpu().numpy()
+    rng = np.random.default_rng(3)
+    fb = np.nonzero(dstat != oracle.BP_OK)[0]
+    pick = [rng.choice(B, 120, replace=False)]
+    for c in range(len(ocodes)):
+        pick.append(fb[code_of[fb] == c][:3])
+    sample = np.unique(np.concatenate(pick))
+    sub_off = np.zeros(len(sample), np.int64)
+    sizes = np.array([ocodes[c].N for c in code_of[sample]], np.int64)
+    sub_off[1:] = np.cumsum(sizes)[:-1]
+    sub_llr = np.concatenate([llr[off[b]:off[b] + ocodes[code_of[b]].N] for b in sample])
+    ref = reference(ocodes, code_of[sample], sub_off, sub_llr, 200, 8, "f16")
+    check(ocodes, code_of[sample], dec.bits.cpu().numpy()[sample], dstat[sample],
+          dec.iters.cpu().numpy().astype(np.int32)[sample], ref)
+    assert len(fb) > 1000 and set(np.unique(dstat)) <= {1, 2, 3}
