@@ -21,8 +21,10 @@ Other workloads (`--workload`, one JSON line each, same keys):
           CA-SCL L = 32; reports the CA-SCL share of the runtime and the batch latency p50/p99.
   paper   the paper's own configuration: N = 4096, K = 2048 (incl. CRC-16), BP with the exact PE
           function in FP32 (clip 20), i_max = 50, CA-SCL L = 32, swept over Eb/N0 (FER, BER,
-          fallback rate, throughput and batch latency per point, min-sum FP32 and half2 beside);
-          `value` is the largest exact-g throughput of the sweep, the quantity the paper reports.
+          fallback rate, throughput and batch latency per point, min-sum FP32 and half2 beside,
+          and CA-SCL alone on every frame -- the paper's non-hybrid decoder -- with the hybrid's
+          speed-up over it); `value` is the largest exact-g throughput of the sweep, the quantity
+          the paper reports.
 """
 from __future__ import annotations
 
@@ -854,6 +856,21 @@ def run_paper(a, world, rank, local):
                 ops = float((6 * code.n * N + code.K) * it.sum()) * steps
                 r["roofline"] = _alu_roofline(ops, bp_ms, prec == api.POLAR_FP16, dev)
             pt[name] = r
+        # CA-SCL alone on every frame (the paper's non-hybrid reference decoder): the hybrid's
+        # speed-up over it at this Eb/N0
+        for _ in range(max(a.warmup, 1)):
+            dec.scl(llr)
+        torch.cuda.synchronize()
+        api.polar_profile_enable(True)
+        ms_s, _ = _timed(lambda: dec.scl(llr), steps, stream, local, dist)
+        api.polar_profile_enable(False)
+        _, _, scl_only_ms, scl_n = api.polar_profile_read()
+        launches += scl_n
+        ferr, _ = _popcount_errors(dec.bits, payload)
+        scl_gbit = world * P * B * steps / (ms_s * 1e-3) / 1e9
+        pt["scl_only"] = {"gbit_s": scl_gbit, "ms_per_step": ms_s / steps, "fer": float(ferr.float().mean().item()),
+                          "hybrid_speedup_exact_g": pt["exact_g"]["gbit_s"] / scl_gbit,
+                          "hybrid_speedup_min_sum_fp16": pt["min_sum_fp16"]["gbit_s"] / scl_gbit}
         points.append(pt)
     best = max(points, key=lambda p: p["exact_g"]["gbit_s"])
     value = best["exact_g"]["gbit_s"]
