@@ -845,9 +845,9 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
 // of a mixed batch (-1: the batch's single code): plan of the code, the list's shared words `ws`
 // and global slot `slot` (null: every level in shared memory).  A list without a frame still walks
 // the code's structure with no path, so both lists of a warp must be given the same code.
-template <bool TWO, int W>
+template <bool TWO, int W, bool MW = false>
 __device__ __forceinline__ void scl_warp_frame(const SCLArgs& a, int frame, int code_id, uint32_t* ws, float* slot,
-                                               uint8_t* selc)
+                                               uint8_t* selc, uint32_t* ptab = nullptr)
 {
     constexpr int LISTS = 32 / W;
     const int L = a.L;
@@ -867,7 +867,7 @@ __device__ __forceinline__ void scl_warp_frame(const SCLArgs& a, int frame, int 
     S.stage = S.sA + scl_smem_llr_words(S.KS, L);
     S.gA = slot;
     S.gC = slot ? reinterpret_cast<uint32_t*>(slot + (size_t)L * (C.N - (2 << S.KS))) : nullptr;
-    scl_decode_frame<TWO, W>(a, C, frame, S, selc);
+    scl_decode_frame<TWO, W, MW>(a, C, frame, S, selc, ptab);
 }
 
 // W = 32: one frame per warp; W = 16: two (one per half-warp list), claimed together.  In a mixed
@@ -893,27 +893,16 @@ __global__ void __launch_bounds__(kSclWarpsPerCTA * 32) scl_kernel(const SCLArgs
         // hold the shared path pointers), which shortens the frame's decoding latency.
         if (!a.code_of && count <= (int)gridDim.x && blockDim.x >= 64) {
             uint32_t* ptab = smem + a.warp_words;
+            // warp 0's list words, list-step scratch and global slot serve the CTA's frame
+            float* slot0 = a.scratch ? a.scratch + (size_t)blockIdx.x * (blockDim.x >> 5) * (size_t)a.slot_words : nullptr;
+            uint8_t* selc0 = reinterpret_cast<uint8_t*>(smem + a.warp_words - 16);
             for (;;) {
                 if (threadIdx.x == 0) ptab[100] = (uint32_t)atomicAdd(a.next, 1);
                 __syncthreads();
                 const int idx = (int)ptab[100];
                 __syncthreads();
                 if (idx >= count) break;  // uniform over the CTA
-                const int frame = a.list ? a.list[idx] : idx;
-                SCLWarp S;
-                S.L = a.L;
-                S.KS = a.KS;
-                S.KC = a.KC;
-                uint32_t* ws0 = smem;  // warp 0's list words
-                S.sC = ws0;
-                S.sA = reinterpret_cast<float*>(ws0 + scl_smem_c_words(S.KC, a.L));
-                S.stage = S.sA + scl_smem_llr_words(S.KS, a.L);
-                float* slot0 = a.scratch ? a.scratch + ((size_t)blockIdx.x * (blockDim.x >> 5) * LISTS) * (size_t)a.slot_words
-                                         : nullptr;
-                S.gA = slot0;
-                S.gC = slot0 ? reinterpret_cast<uint32_t*>(slot0 + (size_t)a.L * (a.code->N - (2 << S.KS))) : nullptr;
-                scl_decode_frame<TWO, W, true>(a, *a.code, frame, S, reinterpret_cast<uint8_t*>(smem + a.warp_words - 16),
-                                               ptab);
+                scl_warp_frame<TWO, W, true>(a, a.list ? a.list[idx] : idx, -1, smem, slot0, selc0, ptab);
                 __syncthreads();
             }
             return;
