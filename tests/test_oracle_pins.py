@@ -303,7 +303,8 @@ def test_round_half_matches_ieee_binary16():
                                    3 * 2.0 ** -26, 1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11])])
     xs = xs.astype(np.float32)
     for v in xs:
-        ref = float(np.float16(v))
+        with np.errstate(over="ignore"):  # 65520 rounds to infinity in binary16, as intended
+            ref = float(np.float16(v))
         got = oracle.round_half(float(v))
         assert (got == ref) or (math.isinf(ref) and math.isinf(got)), (v, got, ref)
 
