@@ -700,11 +700,16 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
         for (int r = 0; r < 32; ++r) {
             const uint32_t col = C.colsyn[blk * 32 + r];
             float lam = 0.0f;
-            switch (r) {
+            if (r & 1) {
+                // odd bits (half of them): one g from level 1, no dispatch
+                lam = scl_g(lf.l1[0], lf.l1[1], lf.c[0] & 1u);
+            } else {
+                switch (r) {
 #define SCL_LEAF_LLR(R) \
-    case R: lam = leaf_llr<R>(lf); break;
-                SCL_FOR_32(SCL_LEAF_LLR)
+    case 2 * (R): lam = leaf_llr<2 * (R)>(lf); break;
+                    SCL_FOR_8(SCL_LEAF_LLR, 0) SCL_FOR_8(SCL_LEAF_LLR, 8)
 #undef SCL_LEAF_LLR
+                }
             }
             uint32_t bitv = 0u;
             bool moved = false;
