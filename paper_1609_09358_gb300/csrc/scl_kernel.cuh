@@ -336,6 +336,10 @@ __device__ __forceinline__ float leaf_llr(Leaf& f)
 // switch on r; the LLR step keeps the switch, which measured faster than its runtime form).
 __device__ __forceinline__ uint32_t leaf_psum_rt(Leaf& f, uint32_t bitv, int r)
 {
+    if (!(r & 1)) {  // even bits (half of them): the bit itself is the level-0 partial sum
+        f.c[0] = bitv;
+        return bitv;
+    }
     const int kc = __ffs(~r) - 1;
     uint32_t v = bitv;
     if (kc > 0) v = ((v ^ f.c[0]) & 0x1u) | ((v & 0x1u) << 1);
@@ -703,11 +707,15 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             if (r & 1) {
                 // odd bits (half of them): one g from level 1, no dispatch
                 lam = scl_g(lf.l1[0], lf.l1[1], lf.c[0] & 1u);
+            } else if ((r & 3) == 2) {
+                // bits 2 mod 4 (a quarter): g into level 1, then f
+                leaf_g<2>(lf.l2, lf.l1, lf.c[1]);
+                lam = xmin(lf.l1[0], lf.l1[1]);
             } else {
                 switch (r) {
 #define SCL_LEAF_LLR(R) \
-    case 2 * (R): lam = leaf_llr<2 * (R)>(lf); break;
-                    SCL_FOR_8(SCL_LEAF_LLR, 0) SCL_FOR_8(SCL_LEAF_LLR, 8)
+    case 4 * (R): lam = leaf_llr<4 * (R)>(lf); break;
+                    SCL_FOR_8(SCL_LEAF_LLR, 0)
 #undef SCL_LEAF_LLR
                 }
             }
