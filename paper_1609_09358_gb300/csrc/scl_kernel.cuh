@@ -340,6 +340,11 @@ __device__ __forceinline__ uint32_t leaf_psum_rt(Leaf& f, uint32_t bitv, int r)
         f.c[0] = bitv;
         return bitv;
     }
+    if (!(r & 2)) {  // bits 1 mod 4 (a quarter): one fold into level 1
+        const uint32_t v1 = ((bitv ^ f.c[0]) & 0x1u) | ((bitv & 0x1u) << 1);
+        f.c[1] = v1;
+        return v1;
+    }
     const int kc = __ffs(~r) - 1;
     uint32_t v = bitv;
     if (kc > 0) v = ((v ^ f.c[0]) & 0x1u) | ((v & 0x1u) << 1);
@@ -711,11 +716,16 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                 // bits 2 mod 4 (a quarter): g into level 1, then f
                 leaf_g<2>(lf.l2, lf.l1, lf.c[1]);
                 lam = xmin(lf.l1[0], lf.l1[1]);
+            } else if ((r & 7) == 4) {
+                // bits 4 mod 8 (an eighth): g into level 2, then f twice
+                leaf_g<4>(lf.l3, lf.l2, lf.c[2]);
+                leaf_f<2>(lf.l2, lf.l1);
+                lam = xmin(lf.l1[0], lf.l1[1]);
             } else {
                 switch (r) {
 #define SCL_LEAF_LLR(R) \
-    case 4 * (R): lam = leaf_llr<4 * (R)>(lf); break;
-                    SCL_FOR_8(SCL_LEAF_LLR, 0)
+    case 8 * (R): lam = leaf_llr<8 * (R)>(lf); break;
+                    SCL_LEAF_LLR(0) SCL_LEAF_LLR(1) SCL_LEAF_LLR(2) SCL_LEAF_LLR(3)
 #undef SCL_LEAF_LLR
                 }
             }
