@@ -775,17 +775,47 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                 const int Wk = 1 << (k - 5), total = act * Wk, tmax = act_both2 * Wk;
                 const uint32_t* ckb = S.Cl(k);
                 const uint32_t my_k = fld(pC, k);
-                for (int e0 = 0; e0 < tmax; e0 += W) {
-                    const int e = e0 + lane;
-                    const int p = (e / Wk) & (W - 1);
-                    const uint32_t pd = sg.shfl(my_dst, p);
-                    const uint32_t pk = sg.shfl(my_k, p);
-                    if (e < total) {
-                        const int w = e % Wk;
-                        uint32_t* dst = dstl + pd * cwk;
-                        const uint32_t x = dst[w];
-                        dst[Wk + w] = x;
-                        dst[w] = x ^ ckb[pk * scl_cs(k) + w];
+                if constexpr (W == 32) {
+                    // four elements per lane and round, loads first and unconditional (an element
+                    // past the list reads a word of a valid array), stores predicated
+                    constexpr int UC = 4;
+                    for (int e0 = 0; e0 < tmax; e0 += UC * W) {
+                        uint32_t xv[UC], cv[UC], pdv[UC];
+#pragma unroll
+                        for (int q = 0; q < UC; ++q) {
+                            const int e = e0 + W * q + lane;
+                            const int p = (e >> (k - 5)) & (W - 1);
+                            const int w = e & (Wk - 1);
+                            pdv[q] = sg.shfl(my_dst, p);
+                            xv[q] = dstl[pdv[q] * cwk + w];
+                            cv[q] = ckb[sg.shfl(my_k, p) * scl_cs(k) + w];
+                        }
+#pragma unroll
+                        for (int q = 0; q < UC; ++q) {
+                            const int e = e0 + W * q + lane;
+                            if (e < total) {
+                                uint32_t* dst = dstl + pdv[q] * cwk;
+                                const int w = e & (Wk - 1);
+                                dst[Wk + w] = xv[q];
+                                dst[w] = xv[q] ^ cv[q];
+                            }
+                        }
+                    }
+                } else {
+                    // half-warp lists: one element per lane (the unrolled form measured slower
+                    // with 2^16 frames, the two lists' registers)
+                    for (int e0 = 0; e0 < tmax; e0 += W) {
+                        const int e = e0 + lane;
+                        const int p = (e >> (k - 5)) & (W - 1);
+                        const uint32_t pd = sg.shfl(my_dst, p);
+                        const uint32_t pk = sg.shfl(my_k, p);
+                        if (e < total) {
+                            const int w = e & (Wk - 1);
+                            uint32_t* dst = dstl + pd * cwk;
+                            const uint32_t x = dst[w];
+                            dst[Wk + w] = x;
+                            dst[w] = x ^ ckb[pk * scl_cs(k) + w];
+                        }
                     }
                 }
                 __syncwarp();
