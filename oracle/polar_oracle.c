@@ -233,7 +233,7 @@ float or_round_half(float x)
 #define OR_BP_G_EXACT 4
 
 /* ------------------------------------------------------------------------------------------ */
-/* Type-generic decoders: BP, SC, SCL, hybrid, in FP32 (bit-exact parity target), FP64 (judge)  */
+/* Type-generic decoders: BP, SC, SCL, hybrid, in FP32 (bit-exact parity target), FP64 (FER ref.) */
 /* and FP16-emulated (half-precision BP messages).                                           */
 /* ------------------------------------------------------------------------------------------ */
 #define OR_ROUND(x) (x)
