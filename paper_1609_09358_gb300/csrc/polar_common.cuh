@@ -51,17 +51,36 @@ __device__ __forceinline__ float stage_clip(float v, float m)
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 
+// Base-2 exponential and logarithm of the special-function unit (approximate, subnormals flushed).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Exact PE function g(a, b) = ln((1 + e^(a+b)) / (e^a + e^b)) (Sec. II-B), in the form
-//   sign(a) sign(b) min(|a|, |b|) + ln(1 + e^-|a+b|) - ln(1 + e^-|a-b|)
+//   sign(a) sign(b) min(|a|, |b|) + ln 2 [log2(1 + 2^-|s|) - log2(1 + 2^-|d|)],
+//   s = (a + b) log2 e, d = (a - b) log2 e
 // (the same function: the LLR of the XOR of two independent bits), whose exponentials never
-// overflow.  The two corrections use the fast exponential and logarithm (absolute error of a few
-// 1e-7 on the clipped magnitudes), so results agree with the exact value to a tolerance, not to
-// the bit.
+// overflow.  Working in base 2 lets the special-function unit's ex2 / lg2 take the arguments as
+// they are (s, d from one multiply and two fused multiply-adds, the ln 2 folded into the final
+// fused add).  The approximate ex2 / lg2 leave an absolute error of a few 1e-7 on the clipped
+// magnitudes, so results agree with the exact value to a tolerance, not to the bit.
 __device__ __forceinline__ float g_exact(float a, float b)
 {
-    const float cs = __logf(fadd(1.0f, __expf(-fabsf(fadd(a, b)))));
-    const float cd = __logf(fadd(1.0f, __expf(-fabsf(__fsub_rn(a, b)))));
-    return fadd(xmin(a, b), __fsub_rn(cs, cd));
+    const float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
+    const float tb = __fmul_rn(b, kLog2e);
+    const float s = __fmaf_rn(a, kLog2e, tb), d = __fmaf_rn(a, kLog2e, -tb);
+    const float ls = lg2_approx(fadd(1.0f, ex2_approx(-fabsf(s))));
+    const float ld = lg2_approx(fadd(1.0f, ex2_approx(-fabsf(d))));
+    return __fmaf_rn(kLn2, __fsub_rn(ls, ld), xmin(a, b));
 }
 
 // ---------------------------------------------------------------------------- half2 primitives
