@@ -405,6 +405,17 @@ def _timed_variant(a, code, dec, step, payload, stream, dist, max_steps=50):
             "launches_per_step": (bp_n + scl_n) / steps}
 
 
+def _exact_traffic_per_frame(N, K):
+    """DRAM bytes per frame of the exact-g BP kernel from its committed ncu capture (None if absent)."""
+    tfile = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if os.path.exists(tfile):
+        for line in open(tfile):
+            f = line.split()
+            if len(f) >= 3 and f[0] == "bp_kernel_exact" and f[1] == "n%d_k%d" % (N, K):
+                return float(f[2])
+    return None
+
+
 def decision_aided(a, code, llr, payload, stream, dist):
     """Decision-aided CA-SCL (Sec. II-A) on the same frames: the da_bits most reliable information
     positions (Bhattacharyya at the construction's design point) are decided by each path's hard
@@ -848,7 +859,8 @@ def run_paper(a, world, rank, local):
                 peak = sms * (16.0 / 3.0) * sm_max_mhz * 1e6
                 ach = ops / (bp_ms * 1e-3) if bp_ms > 0 else 0.0
                 r["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
-                                 "unit": "T g-evaluations/s", "frac": ach / peak, "traffic": None,
+                                 "unit": "T g-evaluations/s", "frac": ach / peak,
+                                 "traffic": (lambda t: t * B if t else None)(_exact_traffic_per_frame(N, code.K)),
                                  "kernel": "bp_kernel (exact g)",
                                  "peak_basis": "%d SMs x 16/3 g per clock (2 ex2 at 32/clk, 2 lg2 at 16/clk per SM, "
                                                "measured) x %.0f MHz" % (sms, sm_max_mhz)}
