@@ -853,16 +853,16 @@ def run_paper(a, world, rank, local):
                  "batch_latency_ms": {"mean": float(np.mean(lat)), "max": float(np.max(lat))}, "clocks": clocks}
             if name == "exact_g":
                 # the exact PE function is bound by the special-function units: each g takes two
-                # exponentials (32 per clock per SM on this part) and two logarithms (16 per clock),
-                # i.e. at most 16/3 g per clock per SM; 2 n N g per frame-iteration
+                # exponentials (32 per clock per SM on this part) and one logarithm (16 per clock),
+                # i.e. at most 8 g per clock per SM; 2 n N g per frame-iteration
                 ops = 2.0 * code.n * N * float(it.sum()) * steps
-                peak = sms * (16.0 / 3.0) * sm_max_mhz * 1e6
+                peak = sms * 8.0 * sm_max_mhz * 1e6
                 ach = ops / (bp_ms * 1e-3) if bp_ms > 0 else 0.0
                 r["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
                                  "unit": "T g-evaluations/s", "frac": ach / peak,
                                  "traffic": (lambda t: t * B if t else None)(_exact_traffic_per_frame(N, code.K)),
                                  "kernel": "bp_kernel (exact g)",
-                                 "peak_basis": "%d SMs x 16/3 g per clock (2 ex2 at 32/clk, 2 lg2 at 16/clk per SM, "
+                                 "peak_basis": "%d SMs x 8 g per clock (2 ex2 at 32/clk, 1 lg2 at 16/clk per SM, "
                                                "measured) x %.0f MHz" % (sms, sm_max_mhz)}
             else:
                 ops = float((6 * code.n * N + code.K) * it.sum()) * steps

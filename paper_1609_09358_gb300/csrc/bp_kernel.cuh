@@ -430,6 +430,17 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
         else
             return xmin(x, y);
     };
+    // both PE functions of a node pair; the exact form evaluates the two as one packed pair
+    auto gf2 = [&](MSG x1, MSG y1, MSG x2, MSG y2, MSG& o1, MSG& o2) {
+        if constexpr (EXACT) {
+            const float2 g = g_exact2(make_float2(x1, x2), make_float2(y1, y2));
+            o1 = clipm(g.x, a.llr_max);
+            o2 = clipm(g.y, a.llr_max);
+        } else {
+            o1 = gf(x1, y1);
+            o2 = gf(x2, y2);
+        }
+    };
 
     MSG* xbuf = reinterpret_cast<MSG*>(slot_smem);         // [2][XW]
     uint32_t* csyn = slot_smem + 2 * P::XW;                // [R][T]
@@ -552,8 +563,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             for (int k = 0; k < R; ++k) {
                 if (k & dd) continue;
                 const int k2 = k | dd;
-                MSG o1 = gf(Rc[n][k], fadd(Lc[n + 1][k2], Rc[n][k2]));
-                MSG gg = gf(Rc[n][k], Lc[n + 1][k]);
+                MSG o1, gg;
+                gf2(Rc[n][k], fadd(Lc[n + 1][k2], Rc[n][k2]), Rc[n][k], Lc[n + 1][k], o1, gg);
                 if constexpr (WEIGHTED) {
                     // itc of this half was already advanced past the last iteration
                     const MSG w1 = MT::splat(wscalar(it_done - 1, 0, n, k));
@@ -605,8 +616,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                 if (k & dd) continue;
                 const int k2 = k | dd;
                 const MSG a1 = Rc[s][k], a2 = Rc[s][k2], l1 = Lc[s + 1][k], l2 = Lc[s + 1][k2];
-                MSG o1 = gf(a1, fadd(l2, a2));
-                MSG gg = gf(a1, l1);
+                MSG o1, gg;
+                gf2(a1, fadd(l2, a2), a1, l1, o1, gg);
                 if constexpr (WEIGHTED) {
                     o1 = clipm(fmul(wk(wc, k), o1), Mv);
                     gg = fmul(wk(wc, k2), gg);
@@ -647,8 +658,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                 if (k & dd) continue;
                 const int k2 = k | dd;
                 const MSG a1 = Rc[s][k], a2 = Rc[s][k2], l1 = Lc[s + 1][k], l2 = Lc[s + 1][k2];
-                MSG o1 = gf(l1, fadd(l2, a2));
-                MSG gg = gf(a1, l1);
+                MSG o1, gg;
+                gf2(l1, fadd(l2, a2), a1, l1, o1, gg);
                 if constexpr (WEIGHTED) {
                     o1 = clipm(fmul(wk(wc, k), o1), Mv);
                     gg = fmul(wk(wc, k2), gg);
@@ -769,10 +780,19 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
     }
 }
 
+// Resident CTAs per SM that a kernel's register allocation targets: the exact PE function (VAR
+// bit 0) keeps more temporaries live than min-sum and takes the weighted kernels' budget up to
+// N = 1024 (from N = 2048 on, fewer CTAs would leave too few warps per SM).
+template <int LOGN, bool WEIGHTED, int VAR>
+constexpr int bp_min_ctas()
+{
+    return WEIGHTED || ((VAR & 1) && LOGN <= 10) ? BPConfig<LOGN>::MIN_CTAS_W : BPConfig<LOGN>::MIN_CTAS;
+}
+
 // Per-length kernel: F frame groups per CTA; THREADS = F * T (passed explicitly: launch bounds
 // take no dependent member expression).
 template <int LOGN, class MSG, bool WEIGHTED, int THREADS, bool SYNP = false, int VAR = 0>
-__global__ void __launch_bounds__(THREADS, WEIGHTED ? BPConfig<LOGN>::MIN_CTAS_W : BPConfig<LOGN>::MIN_CTAS) bp_kernel(const BPArgs a)
+__global__ void __launch_bounds__(THREADS, bp_min_ctas<LOGN, WEIGHTED, VAR>()) bp_kernel(const BPArgs a)
 {
     using P = typename BPConfig<LOGN>::Plan;
     constexpr int F = BPConfig<LOGN>::F;

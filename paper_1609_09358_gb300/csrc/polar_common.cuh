@@ -66,21 +66,54 @@ __device__ __forceinline__ float lg2_approx(float x)
 }
 
 // Exact PE function g(a, b) = ln((1 + e^(a+b)) / (e^a + e^b)) (Sec. II-B), in the form
-//   sign(a) sign(b) min(|a|, |b|) + ln 2 [log2(1 + 2^-|s|) - log2(1 + 2^-|d|)],
+//   sign(a) sign(b) min(|a|, |b|) + ln(p / q),  p = 1 + 2^-|s|,  q = 1 + 2^-|d|,
 //   s = (a + b) log2 e, d = (a - b) log2 e
 // (the same function: the LLR of the XOR of two independent bits), whose exponentials never
 // overflow.  Working in base 2 lets the special-function unit's ex2 / lg2 take the arguments as
 // they are (s, d from one multiply and two fused multiply-adds, the ln 2 folded into the final
-// fused add).  The approximate ex2 / lg2 leave an absolute error of a few 1e-7 on the clipped
+// fused add).  The quotient costs one logarithm instead of the two of ln p - ln q: 1/q (q in
+// [1, 2]) comes from Newton-Raphson on the FMA pipe, started from the minimax quadratic
+// 70/33 - 16/11 q + 32/99 q^2 (relative error at most 1/99 on [1, 2]) and refined twice by
+// r <- r + r (1 - q r), which squares the relative error each time (1e-4, then ~1e-8).  So the
+// special-function unit does three operations per g: two ex2 (full rate) and one lg2 (half
+// rate).  The approximate ex2 / lg2 leave an absolute error of a few 1e-7 on the clipped
 // magnitudes, so results agree with the exact value to a tolerance, not to the bit.
 __device__ __forceinline__ float g_exact(float a, float b)
 {
     const float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
-    const float tb = __fmul_rn(b, kLog2e);
-    const float s = __fmaf_rn(a, kLog2e, tb), d = __fmaf_rn(a, kLog2e, -tb);
-    const float ls = lg2_approx(fadd(1.0f, ex2_approx(-fabsf(s))));
-    const float ld = lg2_approx(fadd(1.0f, ex2_approx(-fabsf(d))));
-    return __fmaf_rn(kLn2, __fsub_rn(ls, ld), xmin(a, b));
+    const float ta = __fmul_rn(a, kLog2e);
+    const float s = __fmaf_rn(b, kLog2e, ta), d = __fmaf_rn(b, -kLog2e, ta);
+    const float p = fadd(1.0f, ex2_approx(-fabsf(s)));
+    const float nq = __fmaf_rn(ex2_approx(-fabsf(d)), -1.0f, -1.0f);  // -q
+    float r = __fmaf_rn(__fmaf_rn(32.0f / 99.0f, nq, 16.0f / 11.0f), nq, 70.0f / 33.0f);
+    r = __fmaf_rn(r, __fmaf_rn(nq, r, 1.0f), r);
+    r = __fmaf_rn(r, __fmaf_rn(nq, r, 1.0f), r);
+    return __fmaf_rn(kLn2, lg2_approx(__fmul_rn(p, r)), xmin(a, b));
+}
+
+// Two exact PE functions at once, bit for bit the arithmetic of g_exact on each lane: everything
+// but the special-function operations and the final min runs as packed FP32 (fma / add / mul
+// .f32x2, one instruction for both lanes).  Both forms work on nq = -q so that no packed operand
+// needs a negation: the seed becomes 70/33 + 16/11 nq + 32/99 nq^2 and 1 - q r = nq r + 1.
+__device__ __forceinline__ float2 g_exact2(float2 a, float2 b)
+{
+    const float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
+    const float2 one = make_float2(1.0f, 1.0f), mone = make_float2(-1.0f, -1.0f);
+    const float2 ta = __fmul2_rn(a, make_float2(kLog2e, kLog2e));
+    const float2 s = __ffma2_rn(b, make_float2(kLog2e, kLog2e), ta);
+    const float2 d = __ffma2_rn(b, make_float2(-kLog2e, -kLog2e), ta);
+    const float2 xs = make_float2(ex2_approx(-fabsf(s.x)), ex2_approx(-fabsf(s.y)));
+    const float2 xd = make_float2(ex2_approx(-fabsf(d.x)), ex2_approx(-fabsf(d.y)));
+    const float2 p = __fadd2_rn(one, xs);
+    const float2 nq = __ffma2_rn(xd, mone, mone);
+    float2 r = __ffma2_rn(__ffma2_rn(make_float2(32.0f / 99.0f, 32.0f / 99.0f), nq,
+                                     make_float2(16.0f / 11.0f, 16.0f / 11.0f)),
+                          nq, make_float2(70.0f / 33.0f, 70.0f / 33.0f));
+    r = __ffma2_rn(r, __ffma2_rn(nq, r, one), r);
+    r = __ffma2_rn(r, __ffma2_rn(nq, r, one), r);
+    const float2 pr = __fmul2_rn(p, r);
+    return __ffma2_rn(make_float2(kLn2, kLn2), make_float2(lg2_approx(pr.x), lg2_approx(pr.y)),
+                      make_float2(xmin(a.x, b.x), xmin(a.y, b.y)));
 }
 
 // ---------------------------------------------------------------------------- half2 primitives
