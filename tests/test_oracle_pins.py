@@ -266,6 +266,43 @@ def test_bp_first_half_frozen_free_bit():
     assert out["llr_u"][0, 0] == -1.25
 
 
+def _read_bp_cases(golden_dir):
+    cases, cur = [], None
+    for r in _read_golden(golden_dir, "bp_clip_schedule.txt"):
+        f = r.split()
+        if f[0] == "case":
+            kv = dict(x.split("=") for x in f[2:])
+            frozen = [] if kv["frozen"] == "-" else [int(v) for v in kv["frozen"].split(",")]
+            cur = {"name": f[1], "N": int(kv["N"]), "frozen": frozen,
+                   "llr": [float(v) for v in kv["llr"].split(",")], "iters": []}
+            cases.append(cur)
+        else:
+            kv = dict(x.split("=") for x in f[2:])
+            cur["iters"].append((int(f[1]), [float(v) for v in kv["u"].split(",")],
+                                 [float(v) for v in kv["x"].split(",")]))
+    return cases
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_bp_clip_and_sweep_order_hand_computed(golden_dir, precision):
+    """Sec. II-B clips every computed message and the staged channel values to LLR_max = 20: on
+    the hand-worked cases of tests/golden/bp_clip_schedule.txt a sum above 20 (LLR(u1) = 27 of the
+    N = 2 repetition, the R sweep's 35, the staged 25) must come out clipped, and the N = 4 case's
+    three iterations, whose messages change each time, fix the order of the sweeps (the R sweep
+    of iteration t reads the L messages of iteration t - 1)."""
+    cases = _read_bp_cases(golden_dir)
+    assert [c["name"] for c in cases] == ["sum_clipped", "staging_clip", "r_sweep_clip", "schedule"]
+    for c in cases:
+        N = c["N"]
+        code = _code_from(N, [i for i in range(N) if i not in c["frozen"]])
+        lam = np.array([c["llr"]], np.float32)
+        for t, u, x in c["iters"]:
+            out = oracle.bp_decode(lam, code, t, 20.0, precision, early_stop=False)
+            assert out["llr_u"][0].tolist() == u, (c["name"], t, out["llr_u"][0])
+            assert out["llr_x"][0].tolist() == x, (c["name"], t, out["llr_x"][0])
+            assert np.array_equal(out["u_hat"][0], [0 if i in c["frozen"] else int(u[i] < 0) for i in range(N)])
+
+
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_bp_channel_symmetry(precision):
     """Min-sum BP is symmetric: flipping the channel LLRs by a codeword's signs flips every
