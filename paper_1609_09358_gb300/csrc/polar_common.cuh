@@ -48,6 +48,11 @@ __device__ __forceinline__ float stage_clip(float v, float m)
     return fminf(fmaxf(v, -m), m);
 }
 
+// Channel LLR as CA-SCL reads it: NaN is an erasure (0); magnitudes beyond 2^100, +-inf included,
+// saturate at 2^100, above any LLR a channel gives and small enough that no sum of the SC
+// recursion (at most N channel values) or of a path metric (at most N such sums) overflows.
+__device__ __forceinline__ float scl_stage(float v) { return stage_clip(v, 0x1p100f); }
+
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 

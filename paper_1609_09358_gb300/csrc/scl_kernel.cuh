@@ -640,8 +640,9 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
             // unconditional (an element past the list's end reads a valid slot: its path index is
             // below L and its offset below len), so nothing but the stores is predicated and the
             // rounds' independent chains interleave.
-            auto rounds = [&](auto USE_G) {
-                constexpr bool G = decltype(USE_G)::value;
+            // CH: the level reads the channel row, whose values are staged as CA-SCL reads them
+            auto rounds = [&](auto USE_G, auto FROM_CH) {
+                constexpr bool G = decltype(USE_G)::value, CH = decltype(FROM_CH)::value;
                 constexpr int U = kSclUpRound;
                 for (int e0 = 0; e0 < tmax; e0 += U * TW) {
                     float va[U], vb[U];
@@ -656,6 +657,10 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                         const float* src = srcb + ps * (2 * len);
                         va[q] = src[j];
                         vb[q] = src[j + len];
+                        if constexpr (CH) {
+                            va[q] = scl_stage(va[q]);
+                            vb[q] = scl_stage(vb[q]);
+                        }
                         if constexpr (G) vw[q] = cbk[(MW ? ptab[64 + p] : sg.shfl(my_c, p)) * cwk + (j >> 5)];
                     }
 #pragma unroll
@@ -671,10 +676,16 @@ __device__ void scl_decode_frame(const SCLArgs& a, const DevCode& C, int frame, 
                     }
                 }
             };
-            if (use_g)
-                rounds(std::true_type{});
-            else
-                rounds(std::false_type{});
+            if (from_ch) {
+                if (use_g)
+                    rounds(std::true_type{}, std::true_type{});
+                else
+                    rounds(std::false_type{}, std::true_type{});
+            } else if (use_g) {
+                rounds(std::true_type{}, std::false_type{});
+            } else {
+                rounds(std::false_type{}, std::false_type{});
+            }
             if constexpr (MW)
                 __syncthreads();
             else

@@ -230,6 +230,39 @@ def test_scl_larger_list_not_worse():
     assert errs[2] <= errs[1] <= errs[0] and errs[2] < errs[0], errs
 
 
+def test_scl_non_finite_channel_values():
+    """SC and CA-SCL read a NaN channel value as an erasure (0) and saturate a magnitude beyond
+    2^100 (+-inf included) at 2^100: decisions and metrics equal those of the frame with those
+    substitutions made by hand.  A noiseless frame given as +-inf decodes exactly with metric 0,
+    and every path of the final list keeps a finite metric although the wrong paths' g adds
+    opposite infinities (inf - inf would be NaN)."""
+    code = oracle.make_code(64, 32, 8)
+    _, _, llr = _noisy_frames(code, 1.0, 16, 41)
+    rng = np.random.default_rng(41)
+    pos = rng.random(llr.shape) < 0.15
+    sgn = np.where(rng.random(llr.shape) < 0.5, -1.0, 1.0).astype(np.float32)
+    big = np.float32(2.0 ** 100)
+    a_nan, a_zero = llr.copy(), llr.copy()
+    a_nan[pos], a_zero[pos] = np.nan, 0.0
+    a_inf, a_sat = llr.copy(), llr.copy()
+    a_inf[pos], a_sat[pos] = sgn[pos] * np.inf, sgn[pos] * big
+    a_inf[0, 3], a_sat[0, 3] = np.float32(3e38), big
+    for x, y in ((a_nan, a_zero), (a_inf, a_sat)):
+        assert np.array_equal(oracle.sc_decode(x, code), oracle.sc_decode(y, code))
+        for L in (1, 4, 8):
+            rx, ry = oracle.scl_decode(x, code, L), oracle.scl_decode(y, code, L)
+            for k in ("u_hat", "status", "pm"):
+                assert np.array_equal(rx[k], ry[k]), (L, k)
+            assert np.all(np.isfinite(rx["pm"]))
+    pay = inputs.payload_bits(43, 0, 4, code.P)
+    xs = oracle.encode_batch(pay, code)
+    for b in range(4):
+        row = np.where(xs[b] == 1, -np.inf, np.inf).astype(np.float32)
+        lu, lpm, u, ok = oracle.scl_list(row, code, 8)
+        assert ok and np.array_equal(u, oracle.build_u(pay[b], code)) and np.all(np.isfinite(lpm))
+        assert lpm.min() == 0.0 and lpm.max() > 0.0
+
+
 # ------------------------------------------------------------------------------------------ BP
 def _code_from(N, info):
     frozen = np.ones(N, np.uint8)
