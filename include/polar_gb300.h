@@ -8,6 +8,20 @@
  *     scratch they need comes from the caller's `workspace` (size from polar_workspace_bytes).
  *     The library keeps one small static device table of code descriptions (POLAR_MAX_CODES
  *     slots), filled on the first use of a code on a device.
+ *   - State the library keeps across calls (none of it holds frame data):
+ *       * that code table, and per device the cached device address of hybrid_decode_noalloc's
+ *         static scratch array (about 256 KB, held by every GPU that loads the library);
+ *       * per device, non-blocking streams it creates on first use and keeps until exit: two for
+ *         hybrid_decode_host (a second compute stream, a copy stream) and POLAR_SCHED_BP_STREAMS + 1
+ *         for hybrid_decode_scheduled (its BP streams and its CA-SCL stream); every call orders
+ *         them after the caller's stream and the caller's stream after them, so they never run
+ *         ahead of or behind the call;
+ *       * one page-locked host array of per-chunk failure counts for hybrid_decode_scheduled
+ *         (4 bytes per chunk, grown when a call needs more, kept until exit), under a lock;
+ *       * per device and kernel, whether the kernel's shared-memory limit was raised;
+ *       * the mixed BP plan table set by polar_mixed_autotune / polar_mixed_set_plan;
+ *       * per host thread, the last error message and the profiling records of polar_profile_*
+ *         (CUDA events, pooled).
  *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*, NULL = legacy default
  *     stream).  The first call with a new code uploads that code's tables with a copy on
  *     `stream`; make it before any stream capture.
@@ -63,6 +77,14 @@ extern "C" {
  *                        when BP stops */
 #define POLAR_G_EXACT 0x200
 #define POLAR_STOP_REENCODE 0x400
+/* OR into precision with learned weights: the caller vouches that every scale lies in [-1, 1].
+ * Then |w g| <= |g| <= llr_max and the clip of the scaled term is skipped (the result is the
+ * same); with POLAR_FP16 and max_iters <= wms_iters the two frames of a half2 register are also
+ * kept on the same iteration (a frame that stops waits for its partner, and the pair takes its
+ * next two frames together), so that one prepared scale serves both.  Each frame is decoded
+ * exactly as without the flag; only which frames share a register, and when, differs.  Scales
+ * outside [-1, 1] with this flag give unspecified results. */
+#define POLAR_WMS_UNIT 0x800
 
 #define POLAR_OP_BP 0
 #define POLAR_OP_SCL 1
@@ -226,17 +248,26 @@ int hybrid_decode_mixed(const polar_code* codes, int32_t ncodes, const int32_t* 
                         float llr_max, int32_t precision, int32_t L, uint8_t* bits,
                         int32_t row_stride, uint8_t* status, uint16_t* iters, void* workspace,
                         size_t ws_bytes, void* stream);
-/* Autotuner of the mixed BP launch: for the block lengths that have two BP thread plans (256 and
- * 512: 8 or 4 nodes per thread, i.e. twice or half as many frames per CTA) it times the BP launch
- * on this batch with each choice and keeps the fastest for later hybrid_decode_mixed calls of the
- * same precision.  Synchronises `stream`; overwrites the outputs.  Arguments as in
- * hybrid_decode_mixed.  *chosen (host, may be NULL) receives the plan flags (bit 0: N = 256 uses 4
- * nodes per thread, bit 1: N = 512 does), *best_ms the BP time of the chosen plans. */
+/* Autotuner of the mixed BP launch: for each block length of the batch that has two BP thread
+ * plans (256, 512 and 1024: 8 or 4 nodes per thread, i.e. one frame on half or twice as many
+ * threads, so twice or half as many frames per CTA) it times the BP launch on this batch with each
+ * choice, one length at a time (the others at their current choice), and keeps the fastest for
+ * later hybrid_decode_mixed calls of the same precision (a table inside the library, per
+ * precision).  Synchronises `stream`; overwrites the outputs.  Arguments as in
+ * hybrid_decode_mixed.  chosen (host, may be NULL): 13 entries indexed by log2 N, the nodes per
+ * thread chosen for each length in the batch (0 for the others); *best_ms the BP time of the
+ * chosen plans, *default_ms that of the default plans (8 nodes per thread from N = 256 on). */
 int polar_mixed_autotune(const polar_code* codes, int32_t ncodes, const int32_t* code_of,
                          const int64_t* llr_off, const float* llr, int32_t B, int32_t max_iters,
                          float llr_max, int32_t precision, uint8_t* bits, int32_t row_stride,
                          uint8_t* status, uint16_t* iters, void* workspace, size_t ws_bytes,
-                         void* stream, int32_t* chosen, float* best_ms);
+                         void* stream, int32_t* chosen, float* best_ms, float* default_ms);
+
+/* Sets the mixed BP plan of one block length by hand (as polar_mixed_autotune would): N = 2^log2n
+ * decoded with nodes_per_thread nodes per thread (8 or 4 for N = 256, 512 and 1024; 4 for N = 128;
+ * 8 for N = 2048) in later hybrid_decode_mixed calls of this precision.  POLAR_ERR_ARG for a plan
+ * that does not exist. */
+int polar_mixed_set_plan(int32_t log2n, int32_t nodes_per_thread, int32_t precision);
 
 /* hybrid_decode on frames that live in host memory (not a step of the paper; its Sec. III
  * rejects moving SCL to the CPU because of transfer latency, which is what this hides).  The
@@ -283,6 +314,40 @@ int hybrid_decode_scheduled(const polar_code* code, const float* llr, int32_t B,
  * time in milliseconds and the launch count of each kernel kind, and clears the record. */
 int polar_profile_enable(int32_t on);
 int polar_profile_read(double* bp_ms, int32_t* bp_launches, double* scl_ms, int32_t* scl_launches);
+
+/* The PE function of the BP kernels (Sec. II-B, Fig. 2), elementwise, for checking it against a
+ * reference (not a decoding step): out[i] = g(a[i], b[i]), unclipped (the decoders clip it).
+ *   op: POLAR_PE_MINSUM (sign(a) sign(b) min(|a|, |b|), exact in binary32), POLAR_PE_EXACT
+ *   (ln((1 + e^(a+b)) / (e^a + e^b)) with the fast exponential and logarithm, the scalar form) or
+ *   POLAR_PE_EXACT_PACKED (the same arithmetic as two-lane packed instructions, as the FP32 BP
+ *   kernels evaluate it; elements 2i and 2i+1 are one pair).  a, b, out: device float [n], n >= 0.
+ *   Asynchronous on `stream`.  POLAR_ERR_ARG for an unknown op, n < 0 or NULL pointers. */
+#define POLAR_PE_MINSUM 0
+#define POLAR_PE_EXACT 1
+#define POLAR_PE_EXACT_PACKED 2
+int polar_pe_eval(int32_t op, const float* a, const float* b, float* out, int32_t n, void* stream);
+
+/* Issue-rate microbenchmark (measurement only, not a step of the paper): the throughput of one
+ * instruction the BP kernels' roofline rests on, as results of one lane (an f16x2 instruction
+ * counts once) per SM per SM clock, averaged over the SMs.  32 warps per SM each run 8
+ * independent dependency chains of the instruction; every CTA times its loop with clock64().
+ *   op: one of POLAR_RATE_*.  iters >= 1: rounds of the 8 chains per thread (4096 takes about a
+ *   millisecond).  scratch: device, >= polar_pipe_rate_scratch_bytes() bytes, owned by the caller.
+ *   Synchronises `stream`.  POLAR_ERR_ARG for an unknown op, iters < 1 or NULL pointers,
+ *   POLAR_ERR_WORKSPACE for a short scratch.  polar_pipe_rate_scratch_bytes returns 0 if the
+ *   current device cannot be queried. */
+#define POLAR_RATE_MINXORSIGN_F32 0   /* min.xorsign.abs.f32: the min-sum g and the clip */
+#define POLAR_RATE_MINXORSIGN_F16X2 1 /* min.xorsign.abs.f16x2 */
+#define POLAR_RATE_ADD_F32 2          /* add.rn.f32 */
+#define POLAR_RATE_ADD_F16X2 3        /* add.rn.f16x2 */
+#define POLAR_RATE_MUL_F16X2 4        /* mul.rn.f16x2: the learned scales of the half2 kernels */
+#define POLAR_RATE_MIN_F32 5          /* min.f32 */
+#define POLAR_RATE_EX2_F32 6          /* ex2.approx.ftz.f32: the exact PE function */
+#define POLAR_RATE_LG2_F32 7          /* lg2.approx.ftz.f32 */
+#define POLAR_RATE_PRMT 8             /* prmt.b32: byte permute (pairing of half2 values) */
+size_t polar_pipe_rate_scratch_bytes(void);
+int polar_pipe_rate(int32_t op, int32_t iters, void* scratch, size_t scratch_bytes, double* per_sm_clock,
+                    void* stream);
 
 /* hybrid_decode without any device allocation (the paper has no counterpart: this exists for
  * callers that cannot allocate device memory -- for instance a receive chain that must never call

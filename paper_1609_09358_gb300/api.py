@@ -22,6 +22,9 @@ POLAR_FIXED_ITERS = 0x100  # bp_decode: OR into precision to run exactly max_ite
 # function instead of min-sum, and the re-encoding stop (HD(LLR(x)) = HD(LLR(u)) G) instead of the CRC
 POLAR_G_EXACT = 0x200
 POLAR_STOP_REENCODE = 0x400
+# learned scales all within [-1, 1] (set by the binding for such PreparedScales): no clip of the
+# scaled term, and the half2 frames of a register kept on the same iteration when max_iters <= T
+POLAR_WMS_UNIT = 0x800
 _MSG = 0xFF  # message-type part of precision
 POLAR_OP_BP, POLAR_OP_SCL, POLAR_OP_HYBRID, POLAR_OP_HYBRID_HOST, POLAR_OP_HYBRID_SCHED = 0, 1, 2, 3, 4
 POLAR_SCHED_BP_STREAMS = 3
@@ -72,13 +75,18 @@ SIGNATURES = {
     "hybrid_decode_mixed": (ctypes.c_int, [_CP, _i32, _vp, _vp, _vp, _i32, _i32, _f32, _i32, _i32, _vp, _i32, _vp, _vp,
                                            _vp, _sz, _vp]),
     "polar_mixed_autotune": (ctypes.c_int, [_CP, _i32, _vp, _vp, _vp, _i32, _i32, _f32, _i32, _vp, _i32, _vp, _vp,
-                                            _vp, _sz, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_f32)]),
+                                            _vp, _sz, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_f32),
+                                            ctypes.POINTER(_f32)]),
+    "polar_mixed_set_plan": (ctypes.c_int, [_i32, _i32, _i32]),
     "polar_profile_enable": (ctypes.c_int, [_i32]),
     "polar_profile_read": (ctypes.c_int, [ctypes.POINTER(_f64), ctypes.POINTER(_i32), ctypes.POINTER(_f64),
                                           ctypes.POINTER(_i32)]),
     "polar_workspace_bytes": (_sz, [_CP, _i32, _i32, _i32]),
     "polar_hybrid_fallback_count": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), _vp]),
     "polar_last_error": (ctypes.c_char_p, []),
+    "polar_pe_eval": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _vp]),
+    "polar_pipe_rate_scratch_bytes": (_sz, []),
+    "polar_pipe_rate": (ctypes.c_int, [_i32, _i32, _vp, _sz, ctypes.POINTER(_f64), _vp]),
 }
 
 
@@ -263,37 +271,44 @@ def wms_prepare(code: PolarCode, w, precision: int, prepared, stream=None) -> No
 
 class PreparedScales:
     """Learned weights rewritten once into the decoder's layout and precision (wms_prepare);
-    pass as `wms_scales` to the decoding calls of the same block length and precision."""
+    pass as `wms_scales` to the decoding calls of the same block length and precision.  `unit`:
+    whether every scale lies in [-1, 1] (None: read from w once, here); decoding calls with such
+    scales pass POLAR_WMS_UNIT."""
 
-    def __init__(self, code: PolarCode, w, precision: int, stream=None):
+    def __init__(self, code: PolarCode, w, precision: int, stream=None, unit=None):
         import torch
         if tuple(w.shape[1:]) != (2, code.n, code.N) or w.dtype != torch.float32 or not w.is_cuda:
             raise PolarError("weights must be a CUDA float32 tensor [T][2][n][N]")
         self.N, self.iters, self.precision = code.N, int(w.shape[0]), precision
+        self.unit = bool(w.abs().max().item() <= 1.0) if unit is None else bool(unit)
         self.buf = torch.empty(wms_prepared_bytes(code, self.iters, precision), dtype=torch.uint8, device=w.device)
         self._w = w.contiguous()  # read by the queued prepare kernel
         wms_prepare(code, self._w, precision, self.buf, stream)
 
 
 def _scales(code: PolarCode, wms_scales, precision: int, stream):
-    """(pointer, iterations, keep-alive) of the wms_scales argument of a decoding call: None, a
-    PreparedScales of this length and precision, or natural-layout weights prepared for this call."""
+    """(pointer, iterations, keep-alive, precision flags) of the wms_scales argument of a decoding
+    call: None, a PreparedScales of this length and precision, or natural-layout weights prepared
+    for this call; POLAR_WMS_UNIT is added for scales within [-1, 1]."""
     if wms_scales is None:
-        return None, 0, None
+        return None, 0, None, precision
+    msg = precision & _MSG
     if not isinstance(wms_scales, PreparedScales):
-        wms_scales = PreparedScales(code, wms_scales, precision, stream)
+        wms_scales = PreparedScales(code, wms_scales, msg, stream)
         if stream is not None:
             wms_scales.buf.record_stream(stream)
-    if wms_scales.N != code.N or wms_scales.precision != precision:
+    if wms_scales.N != code.N or wms_scales.precision != msg:
         raise PolarError("prepared weights are for N = %d, precision %d" % (wms_scales.N, wms_scales.precision))
-    return wms_scales.buf.data_ptr(), wms_scales.iters, wms_scales
+    if wms_scales.unit:
+        precision |= POLAR_WMS_UNIT
+    return wms_scales.buf.data_ptr(), wms_scales.iters, wms_scales, precision
 
 
 def bp_decode(code: PolarCode, llr, max_iters: int, llr_max: float, precision: int, wms_scales, bits, status,
               iters, llr_u=None, llr_x=None, workspace=None, stream=None) -> None:
     """wms_scales: None, PreparedScales, or CUDA float32 weights [T][2][n][N] (prepared per call)."""
     B = llr.shape[0]
-    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision & _MSG, stream)
+    wms_scales, w_iters, _keep, precision = _scales(code, wms_scales, precision, stream)
     ws_b = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(load().bp_decode(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, wms_scales, w_iters,
                             _ptr(bits), _ptr(status), _ptr(iters), _ptr(llr_u), _ptr(llr_x), _ptr(workspace), ws_b,
@@ -310,7 +325,7 @@ def scl_decode(code: PolarCode, llr, L: int, bits, status, workspace, stream=Non
 def hybrid_decode(code: PolarCode, llr, max_iters: int, llr_max: float, precision: int, wms_scales, L: int, bits,
                   status, iters, workspace, stream=None) -> None:
     B = llr.shape[0]
-    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision & _MSG, stream)
+    wms_scales, w_iters, _keep, precision = _scales(code, wms_scales, precision, stream)
     ws_b = workspace.numel() * workspace.element_size()
     _check(load().hybrid_decode(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, wms_scales, w_iters,
                                 L, _ptr(bits), _ptr(status), _ptr(iters), _ptr(workspace), ws_b, _stream(stream)),
@@ -324,7 +339,7 @@ def hybrid_decode_host(code: PolarCode, llr_host, max_iters: int, llr_max: float
     for t in (llr_host, bits_host, status_host, iters_host):
         if t.is_cuda or not t.is_contiguous():
             raise PolarError("hybrid_decode_host expects contiguous host tensors")
-    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision & _MSG, stream)
+    wms_scales, w_iters, _keep, precision = _scales(code, wms_scales, precision, stream)
     ws_b = workspace.numel() * workspace.element_size()
     _check(load().hybrid_decode_host(code.ref(), llr_host.data_ptr(), B, max_iters, llr_max, precision,
                                      wms_scales, w_iters, L, bits_host.data_ptr(), status_host.data_ptr(),
@@ -338,7 +353,7 @@ def hybrid_decode_scheduled(code: PolarCode, llr, max_iters: int, llr_max: float
     on the chunks' failures when idle); device tensors as hybrid_decode, workspace of
     POLAR_OP_HYBRID_SCHED size.  Blocks the calling thread until every BP launch has finished."""
     B = llr.shape[0]
-    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision & _MSG, stream)
+    wms_scales, w_iters, _keep, precision = _scales(code, wms_scales, precision, stream)
     ws_b = workspace.numel() * workspace.element_size()
     _check(load().hybrid_decode_scheduled(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, wms_scales,
                                           w_iters, L, chunk, _ptr(bits), _ptr(status), _ptr(iters), _ptr(workspace),
@@ -352,10 +367,39 @@ def hybrid_decode_noalloc(code: PolarCode, llr, max_iters: int, llr_max: float, 
     library's static scratch array is used instead (B <= 65536 frames, CA-SCL list in shared
     memory).  Calls that overlap on the GPU race on that array."""
     B = llr.shape[0]
-    wms_scales, w_iters, _keep = _scales(code, wms_scales, precision & _MSG, stream)
+    wms_scales, w_iters, _keep, precision = _scales(code, wms_scales, precision, stream)
     _check(load().hybrid_decode_noalloc(code.ref(), _ptr(llr), B, max_iters, llr_max, precision, wms_scales,
                                         w_iters, L, _ptr(bits), _ptr(status), _ptr(iters), _stream(stream)),
            "hybrid_decode_noalloc")
+
+
+POLAR_PE_MINSUM, POLAR_PE_EXACT, POLAR_PE_EXACT_PACKED = 0, 1, 2
+
+
+def polar_pe_eval(op: int, a, b, out, stream=None) -> None:
+    """out = g(a, b) elementwise with the BP kernels' PE function (CUDA float32 tensors, unclipped)."""
+    n = a.numel()
+    if b.numel() != n or out.numel() != n:
+        raise PolarError("polar_pe_eval: a, b and out must have the same size")
+    _check(load().polar_pe_eval(op, _ptr(a), _ptr(b), _ptr(out), n, _stream(stream)), "polar_pe_eval")
+
+
+# issue-rate microbenchmark ops (polar_pipe_rate)
+PIPE_RATE_OPS = {"min.xorsign.abs.f32": 0, "min.xorsign.abs.f16x2": 1, "add.rn.f32": 2, "add.rn.f16x2": 3,
+                 "mul.rn.f16x2": 4, "min.f32": 5, "ex2.approx.ftz.f32": 6, "lg2.approx.ftz.f32": 7, "prmt.b32": 8}
+
+
+def polar_pipe_rate(op: int, iters: int, scratch, stream=None) -> float:
+    """Results of one lane per SM per SM clock of instruction `op` (a PIPE_RATE_OPS value);
+    scratch: a CUDA byte tensor of polar_pipe_rate_scratch_bytes() bytes.  Synchronises the stream."""
+    out = _f64(0.0)
+    _check(load().polar_pipe_rate(op, iters, _ptr(scratch), scratch.numel() * scratch.element_size(),
+                                  ctypes.byref(out), _stream(stream)), "polar_pipe_rate")
+    return float(out.value)
+
+
+def polar_pipe_rate_scratch_bytes() -> int:
+    return int(load().polar_pipe_rate_scratch_bytes())
 
 
 def polar_profile_enable(on: bool) -> None:
@@ -448,16 +492,23 @@ def hybrid_decode_mixed(codes, code_of, llr_off, llr, max_iters: int, llr_max: f
 
 
 def polar_mixed_autotune(codes, code_of, llr_off, llr, max_iters: int, llr_max: float, precision: int, bits, status,
-                         iters, workspace, stream=None):
+                         iters, workspace, stream=None) -> dict:
+    """{"nodes_per_thread": {N: nodes per thread chosen}, "bp_ms": BP time with the chosen plans,
+    "bp_ms_default_plans": with the default plans}."""
     arr = _code_array(codes)
     B = code_of.shape[0]
     ws_b = workspace.numel() * workspace.element_size()
-    chosen, best = _i32(0), _f32(0)
+    chosen, best, base = (_i32 * 13)(), _f32(0), _f32(0)
     _check(load().polar_mixed_autotune(arr, len(codes), _ptr(code_of), _ptr(llr_off), _ptr(llr), B, max_iters,
                                        llr_max, precision, _ptr(bits), bits.shape[1], _ptr(status), _ptr(iters),
-                                       _ptr(workspace), ws_b, _stream(stream), ctypes.byref(chosen),
-                                       ctypes.byref(best)), "polar_mixed_autotune")
-    return int(chosen.value), float(best.value)
+                                       _ptr(workspace), ws_b, _stream(stream), chosen, ctypes.byref(best),
+                                       ctypes.byref(base)), "polar_mixed_autotune")
+    plans = {1 << n: int(chosen[n]) for n in range(13) if chosen[n]}
+    return {"nodes_per_thread": plans, "bp_ms": float(best.value), "bp_ms_default_plans": float(base.value)}
+
+
+def polar_mixed_set_plan(N: int, nodes_per_thread: int, precision: int) -> None:
+    _check(load().polar_mixed_set_plan(int(N).bit_length() - 1, nodes_per_thread, precision), "polar_mixed_set_plan")
 
 
 class MixedDecoder:

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpolar_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = ["bp_launch_fp32.cu", "bp_launch_fp32x.cu", "bp_launch_fp16.cu", "mixed_launch.cu", "scl_launch.cu",
-         "polar_api.cu"]
+         "polar_api.cu", "pipe_rates.cu"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 

@@ -407,7 +407,17 @@ __host__ __device__ constexpr uint32_t pe_low_mask(int dd)
     return m;
 }
 
-template <class P, class MSG, bool WEIGHTED, bool SHARED_CTA, class Src, bool SYNP = false, int VAR = 0>
+// register index of the i-th PE of a stage whose partner registers are dd apart: i with a zero
+// bit inserted at dd's position
+__host__ __device__ constexpr int pe_k(int dd, int i) { return ((i & ~(dd - 1)) << 1) | (i & (dd - 1)); }
+
+// WEIGHTED: 0 plain min-sum; 1 learned scales; 2 learned scales within [-1, 1] (|w g| <= |g| <= M,
+// so the scaled term needs no clip) and, for half2, both frames of a register kept on the same
+// iteration (a frame that stops waits for its partner; the pair refills together), so that one
+// binary16 scale, duplicated in the register, scales both -- used when every iteration is a
+// learned one.  (Scales stored as ready (w, w) pairs instead measured slower: twice the bytes
+// read from L2 per frame pair and iteration, which is what bounds the weighted kernel.)
+template <class P, class MSG, int WEIGHTED, bool SHARED_CTA, class Src, bool SYNP = false, int VAR = 0>
 __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, int slot, int t, uint32_t* slot_smem,
                                              Src& src)
 {
@@ -420,6 +430,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
     // every read of its previous contents
     static_assert(P::xidx_l(0) % 2 == 0, "odd number of exchanges per iteration");
     constexpr bool EXACT = (VAR & 1) != 0, REENC = (VAR & 2) != 0;
+    constexpr bool UNIT = WEIGHTED == 2, ALIGNED = UNIT && FPT == 2;
     static_assert(VAR == 0 || (FPT == 1 && !WEIGHTED), "exact g and the re-encoding stop: FP32, unweighted");
     static_assert(!REENC || (T % 32 == 0 && (!SHARED_CTA || T == 32)), "re-encoding vote: whole warps, own barrier");
     // PE function: min-sum (one instruction) or exact; the exact value is clipped like every
@@ -439,6 +450,21 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
         } else {
             o1 = gf(x1, y1);
             o2 = gf(x2, y2);
+        }
+    };
+
+    // FP32 without learned weights: the PEs of a stage are processed two at a time, so that each
+    // of the two additions of a PE pair runs as one packed instruction (add.rn.f32x2, rounded
+    // like the scalar add: the results are the same bits); the comparisons stay scalar.  Not for
+    // the re-encoding stop, whose kernels spill more with the pairs and measured slower.
+    constexpr bool PAIRS = FPT == 1 && !WEIGHTED && !REENC;
+    // g of two PEs: o = (g(x.x, y.x), g(x.y, y.y))
+    auto gpair = [&](float2 x, float2 y) -> float2 {
+        if constexpr (EXACT) {
+            const float2 g = g_exact2(x, y);
+            return make_float2(clipm(g.x, a.llr_max), clipm(g.y, a.llr_max));
+        } else {
+            return make_float2(xmin(x.x, y.x), xmin(x.y, y.y));
         }
     };
 
@@ -500,16 +526,25 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
     struct WPair {
         Row h[FPT];
     };
-    auto wload = [&](int dir, int s) -> WPair {
-        WPair r;
+    // ALIGNED: one row of scales for both halves, at the pair's iteration itp
+    int itp = 0;
+    using WSet = std::conditional_t<ALIGNED, Row, WPair>;
+    auto wload = [&](int dir, int s) -> WSet {
+        WSet r;
+        if constexpr (ALIGNED) {
+            r = itp < a.w_iters ? wms_row<WE, R>(wp + wms_prep_index<P>(itp, dir, s, t, 0)) : wms_ones<WE, R>();
+        } else {
 #pragma unroll
-        for (int h = 0; h < FPT; ++h)
-            r.h[h] = (fr[h] >= 0 && itc[h] < a.w_iters) ? wms_row<WE, R>(wp + wms_prep_index<P>(itc[h], dir, s, t, 0))
-                                                        : wms_ones<WE, R>();
+            for (int h = 0; h < FPT; ++h)
+                r.h[h] = (fr[h] >= 0 && itc[h] < a.w_iters) ? wms_row<WE, R>(wp + wms_prep_index<P>(itc[h], dir, s, t, 0))
+                                                            : wms_ones<WE, R>();
+        }
         return r;
     };
-    auto wk = [&](const WPair& r, int k) -> MSG {
-        if constexpr (FPT == 2)
+    auto wk = [&](const WSet& r, int k) -> MSG {
+        if constexpr (ALIGNED)
+            return __half2half2(r.v[k]);
+        else if constexpr (FPT == 2)
             return __halves2half2(r.h[0].v[k], r.h[1].v[k]);
         else
             return r.h[0].v[k];
@@ -601,7 +636,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
     int it = 0;  // iterations run by this group (selects the partial-syndrome slot parity)
     for (;;) {
         // scales of the stage being computed and of the next one (loaded a stage ahead)
-        WPair wc{}, wn{};
+        WSet wc{}, wn{};
         if constexpr (WEIGHTED) wc = wload(0, 1);
         uint32_t xh = 0;  // re-encoding stop: HD(LLR(x)) of this thread's channel-column nodes
         // ------------------------------------------------------------------ R sweep
@@ -611,22 +646,13 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             constexpr bool cross = P::rcross(s);
             MSG* xb = xbuf + (P::xidx_r(s) & 1) * P::XW;
             if constexpr (WEIGHTED) wn = last ? wload(1, n) : wload(0, s + 1);
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                if (k & dd) continue;
-                const int k2 = k | dd;
-                const MSG a1 = Rc[s][k], a2 = Rc[s][k2], l1 = Lc[s + 1][k], l2 = Lc[s + 1][k2];
-                MSG o1, gg;
-                gf2(a1, fadd(l2, a2), a1, l1, o1, gg);
-                if constexpr (WEIGHTED) {
-                    o1 = clipm(fmul(wk(wc, k), o1), Mv);
-                    gg = fmul(wk(wc, k2), gg);
-                }
-                const MSG o2 = clipm(fadd(gg, a2), Mv);
+            // outputs of the PE (k, k2): R[s+1] registers, the exchange buffer, or (last stage) only
+            // the re-encoding stop's hard decisions of LLR(x)
+            auto emit = [&](int k, int k2, MSG o1, MSG o2) {
                 if constexpr (REENC && last) {
                     // LLR(x) = L[n+1] + R[n+1]: the channel column plus this stage's output
-                    xh |= (MT::neg(fadd(l1, o1), 0) ? 1u : 0u) << k;
-                    xh |= (MT::neg(fadd(l2, o2), 0) ? 1u : 0u) << k2;
+                    xh |= (MT::neg(fadd(Lc[s + 1][k], o1), 0) ? 1u : 0u) << k;
+                    xh |= (MT::neg(fadd(Lc[s + 1][k2], o2), 0) ? 1u : 0u) << k2;
                 }
                 if constexpr (!last) {
                     if constexpr (cross) {
@@ -636,6 +662,33 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                         Rc[s + 1][k] = o1;
                         Rc[s + 1][k2] = o2;
                     }
+                }
+            };
+            if constexpr (PAIRS) {
+#pragma unroll
+                for (int i = 0; i < R / 2; i += 2) {
+                    const int kA = pe_k(dd, i), kB = pe_k(dd, i + 1), kA2 = kA | dd, kB2 = kB | dd;
+                    const float2 a1 = make_float2(Rc[s][kA], Rc[s][kB]);
+                    const float2 a2 = make_float2(Rc[s][kA2], Rc[s][kB2]);
+                    const float2 o1 = gpair(a1, __fadd2_rn(make_float2(Lc[s + 1][kA2], Lc[s + 1][kB2]), a2));
+                    const float2 o2 = __fadd2_rn(gpair(a1, make_float2(Lc[s + 1][kA], Lc[s + 1][kB])), a2);
+                    emit(kA, kA2, o1.x, clipm(o2.x, M));
+                    emit(kB, kB2, o1.y, clipm(o2.y, M));
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    if (k & dd) continue;
+                    const int k2 = k | dd;
+                    const MSG a1 = Rc[s][k], a2 = Rc[s][k2], l1 = Lc[s + 1][k], l2 = Lc[s + 1][k2];
+                    MSG o1, gg;
+                    gf2(a1, fadd(l2, a2), a1, l1, o1, gg);
+                    if constexpr (WEIGHTED) {
+                        o1 = fmul(wk(wc, k), o1);
+                        if constexpr (!UNIT) o1 = clipm(o1, Mv);
+                        gg = fmul(wk(wc, k2), gg);
+                    }
+                    emit(k, k2, o1, clipm(fadd(gg, a2), Mv));
                 }
             }
             if constexpr (cross) {
@@ -653,24 +706,40 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             constexpr bool cross = P::lcross(s);
             MSG* xb = xbuf + (P::xidx_l(s) & 1) * P::XW;
             if constexpr (WEIGHTED && !first) wn = wload(1, s - 1);
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                if (k & dd) continue;
-                const int k2 = k | dd;
-                const MSG a1 = Rc[s][k], a2 = Rc[s][k2], l1 = Lc[s + 1][k], l2 = Lc[s + 1][k2];
-                MSG o1, gg;
-                gf2(l1, fadd(l2, a2), a1, l1, o1, gg);
-                if constexpr (WEIGHTED) {
-                    o1 = clipm(fmul(wk(wc, k), o1), Mv);
-                    gg = fmul(wk(wc, k2), gg);
-                }
-                const MSG o2 = clipm(fadd(gg, l2), Mv);
+            auto emit = [&](int k, int k2, MSG o1, MSG o2) {
                 if constexpr (cross) {
                     xput<P, g>(xb, xbase, t, k, o1);
                     xput<P, g>(xb, xbase, t, k2, o2);
                 } else {
                     Lc[s][k] = o1;
                     Lc[s][k2] = o2;
+                }
+            };
+            if constexpr (PAIRS) {
+#pragma unroll
+                for (int i = 0; i < R / 2; i += 2) {
+                    const int kA = pe_k(dd, i), kB = pe_k(dd, i + 1), kA2 = kA | dd, kB2 = kB | dd;
+                    const float2 l1 = make_float2(Lc[s + 1][kA], Lc[s + 1][kB]);
+                    const float2 l2 = make_float2(Lc[s + 1][kA2], Lc[s + 1][kB2]);
+                    const float2 o1 = gpair(l1, __fadd2_rn(l2, make_float2(Rc[s][kA2], Rc[s][kB2])));
+                    const float2 o2 = __fadd2_rn(gpair(make_float2(Rc[s][kA], Rc[s][kB]), l1), l2);
+                    emit(kA, kA2, o1.x, clipm(o2.x, M));
+                    emit(kB, kB2, o1.y, clipm(o2.y, M));
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    if (k & dd) continue;
+                    const int k2 = k | dd;
+                    const MSG a1 = Rc[s][k], a2 = Rc[s][k2], l1 = Lc[s + 1][k], l2 = Lc[s + 1][k2];
+                    MSG o1, gg;
+                    gf2(l1, fadd(l2, a2), a1, l1, o1, gg);
+                    if constexpr (WEIGHTED) {
+                        o1 = fmul(wk(wc, k), o1);
+                        if constexpr (!UNIT) o1 = clipm(o1, Mv);
+                        gg = fmul(wk(wc, k2), gg);
+                    }
+                    emit(k, k2, o1, clipm(fadd(gg, l2), Mv));
                 }
             }
             if constexpr (cross) {
@@ -693,6 +762,14 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                         memcpy(&ub, &u, 4);
                         asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(m) : "r"(ub));
                         syn0 ^= csyn[k * T + t] & m;
+                    }
+                } else if constexpr (PAIRS) {
+#pragma unroll
+                    for (int k = 0; k < R; k += 2) {
+                        const float2 u = __fadd2_rn(make_float2(Lc[1][k], Lc[1][k + 1]),
+                                                    make_float2(Rc[1][k], Rc[1][k + 1]));
+                        syn0 ^= csyn[k * T + t] & (uint32_t)(__float_as_int(u.x) >> 31);
+                        syn0 ^= csyn[(k + 1) * T + t] & (uint32_t)(__float_as_int(u.y) >> 31);
                     }
                 } else {
 #pragma unroll
@@ -764,17 +841,42 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
         ++it;
         const uint32_t syn[2] = {syn0, syn1};
         bool any = false;
+        if constexpr (ALIGNED) {
+            // a frame that stops is written out and its half idles (its lanes compute values
+            // nobody reads) until the partner stops too; then both refill and restart at 0
+            ++itp;
+            bool pair_done = true;
 #pragma unroll
-        for (int h = 0; h < FPT; ++h) {
-            if (fr[h] < 0) continue;
-            ++itc[h];
-            const bool ok = syn[h] == 0u;
-            const bool stop = REENC ? conv : ok;
-            if ((stop && !a.fixed_iters) || itc[h] >= a.max_iters) {
-                finalize(h, itc[h], ok);
-                refill(h);
+            for (int h = 0; h < FPT; ++h) {
+                if (fr[h] >= 0 && itc[h] >= 0) {
+                    ++itc[h];
+                    const bool ok = syn[h] == 0u;
+                    if ((ok && !a.fixed_iters) || itc[h] >= a.max_iters) {
+                        finalize(h, itc[h], ok);
+                        itc[h] = -1;
+                    }
+                }
+                pair_done &= fr[h] < 0 || itc[h] < 0;
             }
-            any |= fr[h] >= 0;
+            if (pair_done) {
+#pragma unroll
+                for (int h = 0; h < FPT; ++h) refill(h);
+                itp = 0;
+            }
+            any = fr[0] >= 0 || fr[1] >= 0;
+        } else {
+#pragma unroll
+            for (int h = 0; h < FPT; ++h) {
+                if (fr[h] < 0) continue;
+                ++itc[h];
+                const bool ok = syn[h] == 0u;
+                const bool stop = REENC ? conv : ok;
+                if ((stop && !a.fixed_iters) || itc[h] >= a.max_iters) {
+                    finalize(h, itc[h], ok);
+                    refill(h);
+                }
+                any |= fr[h] >= 0;
+            }
         }
         if (!any) break;
     }
@@ -783,15 +885,15 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 // Resident CTAs per SM that a kernel's register allocation targets: the exact PE function (VAR
 // bit 0) keeps more temporaries live than min-sum and takes the weighted kernels' budget up to
 // N = 1024 (from N = 2048 on, fewer CTAs would leave too few warps per SM).
-template <int LOGN, bool WEIGHTED, int VAR>
+template <int LOGN, int WEIGHTED, int VAR>
 constexpr int bp_min_ctas()
 {
-    return WEIGHTED || ((VAR & 1) && LOGN <= 10) ? BPConfig<LOGN>::MIN_CTAS_W : BPConfig<LOGN>::MIN_CTAS;
+    return WEIGHTED != 0 || ((VAR & 1) && LOGN <= 10) ? BPConfig<LOGN>::MIN_CTAS_W : BPConfig<LOGN>::MIN_CTAS;
 }
 
 // Per-length kernel: F frame groups per CTA; THREADS = F * T (passed explicitly: launch bounds
 // take no dependent member expression).
-template <int LOGN, class MSG, bool WEIGHTED, int THREADS, bool SYNP = false, int VAR = 0>
+template <int LOGN, class MSG, int WEIGHTED, int THREADS, bool SYNP = false, int VAR = 0>
 __global__ void __launch_bounds__(THREADS, bp_min_ctas<LOGN, WEIGHTED, VAR>()) bp_kernel(const BPArgs a)
 {
     using P = typename BPConfig<LOGN>::Plan;

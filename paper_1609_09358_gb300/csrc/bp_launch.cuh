@@ -13,12 +13,14 @@ struct BPKernelInfo {
     int groups_per_cta;  // frame groups (frames, or frame pairs for half2) per CTA
 };
 
-// kernel of (log2 N, weighted) for the message type of this translation unit; half2 plain
-// kernels come in a variant with both frames' CRC syndromes in one word (crc_len <= 16)
-BPKernelInfo bp_kernel_info_fp32(int logn, bool weighted);
+// kernel of (log2 N, weighted) for the message type of this translation unit (weighted: 0 plain,
+// 1 learned scales, 2 learned scales within [-1, 1] with both frames of a half2 register on the
+// same iteration -- FP32 takes the form-1 kernel for 2); half2 plain kernels come in a variant
+// with both frames' CRC syndromes in one word (crc_len <= 16)
+BPKernelInfo bp_kernel_info_fp32(int logn, int weighted);
 // FP32 unweighted kernel of a BP variant: bit 0 exact PE function, bit 1 re-encoding stop
 BPKernelInfo bp_kernel_info_fp32_var(int logn, int var);
-BPKernelInfo bp_kernel_info_fp16(int logn, bool weighted, bool packed_syndrome);
+BPKernelInfo bp_kernel_info_fp16(int logn, int weighted, bool packed_syndrome);
 // natural-layout learned weights [iters][2][n][N] -> the prepared layout of the length's plan
 cudaError_t wms_prepare_fp32(int logn, const float* w, int iters, void* out, cudaStream_t st);
 cudaError_t wms_prepare_fp16(int logn, const float* w, int iters, void* out, cudaStream_t st);
@@ -45,7 +47,7 @@ cudaError_t wms_prepare_t(int logn, const float* w, int iters, void* out, cudaSt
 }
 
 template <class MSG>
-BPKernelInfo bp_kernel_info_t(int logn, bool weighted, bool packed_syndrome = false)
+BPKernelInfo bp_kernel_info_t(int logn, int weighted, bool packed_syndrome = false)
 {
     auto pick = [&](auto LOGN_C) -> BPKernelInfo {
         constexpr int LOGN = decltype(LOGN_C)::value;
@@ -58,14 +60,18 @@ BPKernelInfo bp_kernel_info_t(int logn, bool weighted, bool packed_syndrome = fa
             // learned weights: N <= 2048 (no weighted kernel is built for longer codes)
             if constexpr (LOGN > 11)
                 return BPKernelInfo{nullptr, TH, smem, Cfg::F};
+            else if constexpr (std::is_same<MSG, __half2>::value)
+                return BPKernelInfo{weighted == 2 ? (const void*)bp_kernel<LOGN, MSG, 2, TH>
+                                                  : (const void*)bp_kernel<LOGN, MSG, 1, TH>,
+                                    TH, smem, Cfg::F};
             else
-                return BPKernelInfo{(const void*)bp_kernel<LOGN, MSG, true, TH>, TH, smem, Cfg::F};
+                return BPKernelInfo{(const void*)bp_kernel<LOGN, MSG, 1, TH>, TH, smem, Cfg::F};
         }
         if constexpr (std::is_same<MSG, __half2>::value)
-            fn = packed_syndrome ? (const void*)bp_kernel<LOGN, MSG, false, TH, true>
-                                 : (const void*)bp_kernel<LOGN, MSG, false, TH>;
+            fn = packed_syndrome ? (const void*)bp_kernel<LOGN, MSG, 0, TH, true>
+                                 : (const void*)bp_kernel<LOGN, MSG, 0, TH>;
         else
-            fn = (const void*)bp_kernel<LOGN, MSG, false, TH>;
+            fn = (const void*)bp_kernel<LOGN, MSG, 0, TH>;
         return {fn, TH, smem, Cfg::F};
     };
     switch (logn) {
@@ -87,7 +93,7 @@ BPKernelInfo bp_kernel_info_var_t(int logn)
         using P = typename Cfg::Plan;
         constexpr int TH = Cfg::F * P::T;
         const size_t smem = (size_t)Cfg::F * bp_slot_words<P>() * 4;
-        return {(const void*)bp_kernel<LOGN, float, false, TH, false, VAR>, TH, smem, Cfg::F};
+        return {(const void*)bp_kernel<LOGN, float, 0, TH, false, VAR>, TH, smem, Cfg::F};
     };
     switch (logn) {
         case 7: return pick(std::integral_constant<int, 7>{});

@@ -19,10 +19,13 @@ constexpr int kMixMaxCodes = 32;
 constexpr int kMixBlock = 256;
 
 // plan variants: id -> (log2 N, b)
-//   0: (7,2)  1: (8,3)  2: (8,2)  3: (9,3)  4: (9,2)  5: (10,3)  6: (11,3)
-constexpr int kMixVariants = 7;
-__host__ __device__ inline int mix_variant_logn(int v) { return v == 0 ? 7 : v <= 2 ? 8 : v <= 4 ? 9 : v == 5 ? 10 : 11; }
-__host__ __device__ inline int mix_variant_logr(int v) { return (v == 0 || v == 2 || v == 4) ? 2 : 3; }
+//   0: (7,2)  1: (8,3)  2: (8,2)  3: (9,3)  4: (9,2)  5: (10,3)  6: (11,3)  7: (10,2)
+constexpr int kMixVariants = 8;
+__host__ __device__ inline int mix_variant_logn(int v)
+{
+    return v == 0 ? 7 : v <= 2 ? 8 : v <= 4 ? 9 : v == 5 || v == 7 ? 10 : 11;
+}
+__host__ __device__ inline int mix_variant_logr(int v) { return (v == 0 || v == 2 || v == 4 || v == 7) ? 2 : 3; }
 
 struct MixedArgs {
     BPArgs base;                 // llr + llr_off, outputs (fixed row stride), limits, fail list
@@ -61,6 +64,7 @@ inline size_t mix_smem_bytes(int variant)
         case 3: return 4 * (size_t)mix_cta_words<BPPlan<9, 3>>();
         case 4: return 4 * (size_t)mix_cta_words<BPPlan<9, 2>>();
         case 5: return 4 * (size_t)mix_cta_words<BPPlan<10, 3>>();
+        case 7: return 4 * (size_t)mix_cta_words<BPPlan<10, 2>>();
         default: return 4 * (size_t)mix_cta_words<BPPlan<11, 3>>();
     }
 }
@@ -94,6 +98,7 @@ __global__ void __launch_bounds__(kMixBlock, (std::is_same<MSG, float>::value ||
             case 3: mix_run<BPPlan<9, 3>, MSG, SYNP>(m, c, smem); break;
             case 4: mix_run<BPPlan<9, 2>, MSG, SYNP>(m, c, smem); break;
             case 5: mix_run<BPPlan<10, 3>, MSG, SYNP>(m, c, smem); break;
+            case 7: mix_run<BPPlan<10, 2>, MSG, SYNP>(m, c, smem); break;
             default: mix_run<BPPlan<11, 3>, MSG, SYNP>(m, c, smem); break;
         }
         __syncthreads();

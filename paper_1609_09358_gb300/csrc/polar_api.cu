@@ -280,11 +280,14 @@ struct ProfRecord {
 };
 struct ProfState {
     bool on = false;
+    cudaError_t err = cudaSuccess;  // first failed event creation or record since the last read
     std::vector<ProfRecord> recs;
     std::vector<cudaEvent_t> pool;
 };
 static thread_local ProfState g_prof;
 
+// An event from the pool or a new one; null (and the error kept for polar_profile_read) if it
+// cannot be created, in which case the launch goes untimed.
 static cudaEvent_t prof_event()
 {
     if (!g_prof.pool.empty()) {
@@ -293,7 +296,11 @@ static cudaEvent_t prof_event()
         return e;
     }
     cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
+    const cudaError_t rc = cudaEventCreate(&e);
+    if (rc != cudaSuccess) {
+        if (g_prof.err == cudaSuccess) g_prof.err = rc;
+        return nullptr;
+    }
     return e;
 }
 
@@ -304,17 +311,26 @@ struct ProfScope {
     cudaEvent_t start = nullptr;
     ProfScope(int k, cudaStream_t s) : kind(k), st(s)
     {
-        if (g_prof.on) {
-            start = prof_event();
-            cudaEventRecord(start, st);
+        if (g_prof.on && (start = prof_event()) != nullptr) {
+            const cudaError_t rc = cudaEventRecord(start, st);
+            if (rc != cudaSuccess) {
+                if (g_prof.err == cudaSuccess) g_prof.err = rc;
+                g_prof.pool.push_back(start);
+                start = nullptr;
+            }
         }
     }
     ~ProfScope()
     {
-        if (start) {
-            cudaEvent_t stop = prof_event();
-            cudaEventRecord(stop, st);
+        if (!start) return;
+        cudaEvent_t stop = prof_event();
+        const cudaError_t rc = stop ? cudaEventRecord(stop, st) : cudaErrorUnknown;
+        if (rc == cudaSuccess) {
             g_prof.recs.push_back({kind, start, stop});
+        } else {
+            if (stop && g_prof.err == cudaSuccess) g_prof.err = rc;
+            g_prof.pool.push_back(start);
+            if (stop) g_prof.pool.push_back(stop);
         }
     }
 };
@@ -324,7 +340,7 @@ static int bp_variant(int precision)
 {
     return ((precision & POLAR_G_EXACT) ? 1 : 0) | ((precision & POLAR_STOP_REENCODE) ? 2 : 0);
 }
-static int bp_message(int precision) { return precision & ~(POLAR_G_EXACT | POLAR_STOP_REENCODE); }
+static int bp_message(int precision) { return precision & ~(POLAR_G_EXACT | POLAR_STOP_REENCODE | POLAR_WMS_UNIT); }
 
 static int launch_bp(const DevCode* dcode, const polar_code* code, const float* llr, int B, int max_iters,
                      float llr_max, int precision, const void* w, int w_iters, uint8_t* bits, uint8_t* status,
@@ -358,10 +374,14 @@ static int launch_bp(const DevCode* dcode, const polar_code* code, const float* 
     if (w && code->N > POLAR_MAX_N_MIXED)
         return fail(POLAR_ERR_ARG, "learned weights: N = %d > %d", code->N, POLAR_MAX_N_MIXED);
     const int var = bp_variant(precision);
+    const bool unit = (precision & POLAR_WMS_UNIT) != 0;
     precision = bp_message(precision);
-    const BPKernelInfo k = precision == POLAR_FP16 ? bp_kernel_info_fp16(n, w != nullptr, code->crc_len <= 16)
+    // learned scales: the half2 form with both frames of a register on the same iteration when
+    // the caller vouches for scales within [-1, 1] and every iteration is a learned one
+    const int weighted = !w ? 0 : (unit && precision == POLAR_FP16 && max_iters <= w_iters) ? 2 : 1;
+    const BPKernelInfo k = precision == POLAR_FP16 ? bp_kernel_info_fp16(n, weighted, code->crc_len <= 16)
                            : var               ? bp_kernel_info_fp32_var(n, var)
-                                               : bp_kernel_info_fp32(n, w != nullptr);
+                                               : bp_kernel_info_fp32(n, weighted);
     if (!k.fn) return fail(POLAR_ERR_ARG, "no BP kernel for N = %d with these options", code->N);
     if (k.smem > 48 * 1024) {
         // above the default dynamic shared-memory limit (N = 4096); set once per kernel and device
@@ -466,6 +486,25 @@ static std::vector<double> bhattacharyya_lnz(int N, double design_ebn0_db, doubl
         lz.swap(next);
     }
     return lz;
+}
+
+// The PE functions of the BP kernels, elementwise: min-sum, exact (scalar form), exact (the packed
+// pair form the FP32 kernels use; elements 2i and 2i+1 form a pair).  Unclipped.
+__global__ void pe_eval_kernel(int op, const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ out,
+                               int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (op == POLAR_PE_EXACT_PACKED) {
+        const int j = 2 * i;
+        if (j >= n) return;
+        const bool two = j + 1 < n;
+        const float2 r = g_exact2(make_float2(a[j], two ? a[j + 1] : 0.0f), make_float2(b[j], two ? b[j + 1] : 0.0f));
+        out[j] = r.x;
+        if (two) out[j + 1] = r.y;
+        return;
+    }
+    if (i >= n) return;
+    out[i] = op == POLAR_PE_MINSUM ? xmin(a[i], b[i]) : g_exact(a[i], b[i]);
 }
 
 }  // namespace polar
@@ -989,7 +1028,7 @@ int mix_default_variant(int n, int precision)
 {
     std::lock_guard<std::mutex> lock(g_mix_mutex);
     const int v = g_mix_variant[precision][n];
-    if (v) return v;
+    if (v) return v;  // 0 is the default plan of N = 128 as well: no entry needed
     return n == 7 ? 0 : n == 8 ? 1 : n == 9 ? 3 : n == 10 ? 5 : 6;
 }
 
@@ -1127,10 +1166,22 @@ int hybrid_decode_mixed(const polar_code* codes, int32_t ncodes, const int32_t* 
     return e == cudaSuccess ? POLAR_OK : cuda_fail(e, "scl_kernel launch (mixed)");
 }
 
+int polar_mixed_set_plan(int32_t log2n, int32_t nodes_per_thread, int32_t precision)
+{
+    if (precision != POLAR_FP32 && precision != POLAR_FP16) return fail(POLAR_ERR_ARG, "precision = %d", precision);
+    int v = -1;
+    for (int c = 0; c < kMixVariants; ++c)
+        if (mix_variant_logn(c) == log2n && (1 << mix_variant_logr(c)) == nodes_per_thread) v = c;
+    if (v < 0) return fail(POLAR_ERR_ARG, "no mixed BP plan with %d nodes per thread for N = 2^%d", nodes_per_thread, log2n);
+    std::lock_guard<std::mutex> lock(g_mix_mutex);
+    g_mix_variant[precision][log2n] = v;
+    return POLAR_OK;
+}
+
 int polar_mixed_autotune(const polar_code* codes, int32_t ncodes, const int32_t* code_of, const int64_t* llr_off,
                          const float* llr, int32_t B, int32_t max_iters, float llr_max, int32_t precision, uint8_t* bits,
                          int32_t row_stride, uint8_t* status, uint16_t* iters, void* workspace, size_t ws, void* stream,
-                         int32_t* chosen, float* best_ms)
+                         int32_t* chosen, float* best_ms, float* default_ms)
 {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int mr = 0;
@@ -1143,39 +1194,62 @@ int polar_mixed_autotune(const polar_code* codes, int32_t ncodes, const int32_t*
     if ((rc = mix_prepare(codes, ncodes, st, dcodes))) return rc;
     const MixLayout ml = mix_layout(ncodes, B, 0);
     if (!workspace || ws < ml.scratch) return fail(POLAR_ERR_WORKSPACE, "workspace %zu < %zu bytes", ws, ml.scratch);
-    bool has8 = false, has9 = false;
-    for (int c = 0; c < ncodes; ++c) {
-        has8 |= codes[c].N == 256;
-        has9 |= codes[c].N == 512;
+    // plan options per length: the default first, then the alternative with b = 2 (4 nodes per
+    // thread: twice as many threads per frame, half the registers, more column exchanges)
+    int opts[13][2], nopt[13] = {}, pick[13] = {};
+    bool present[13] = {};
+    for (int c = 0; c < ncodes; ++c) present[log2i(codes[c].N)] = true;
+    for (int n = 7; n <= 11; ++n) {
+        opts[n][0] = n == 7 ? 0 : n == 8 ? 1 : n == 9 ? 3 : n == 10 ? 5 : 6;
+        nopt[n] = 1;
+        if (n == 8) opts[n][nopt[n]++] = 2;
+        if (n == 9) opts[n][nopt[n]++] = 4;
+        if (n == 10) opts[n][nopt[n]++] = 7;
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     POLAR_CUDA(cudaEventCreate(&e0));
-    POLAR_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_flags = 0;
-    for (int flags = 0; flags < 4; ++flags) {
-        if (((flags & 1) && !has8) || ((flags & 2) && !has9)) continue;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(POLAR_ERR_CUDA, "cudaEventCreate");
+    }
+    // BP time of the launch with the plans in pick[]: the least of two timed runs after one
+    // untimed run (which also pays any one-time setup)
+    auto time_plans = [&](float* out) -> int {
         int variants[POLAR_MAX_MIX_CODES];
         for (int c = 0; c < ncodes; ++c) {
             const int n = log2i(codes[c].N);
-            variants[c] = n == 7 ? 0 : n == 8 ? ((flags & 1) ? 2 : 1) : n == 9 ? ((flags & 2) ? 4 : 3) : n == 10 ? 5 : 6;
+            variants[c] = opts[n][pick[n]];
         }
         float tmin = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
-            POLAR_CUDA(cudaEventRecord(e0, st));
-            rc = mix_bp(codes, ncodes, dcodes, variants, code_of, llr_off, llr, B, max_iters, llr_max, precision, bits,
-                        row_stride, status, iters, static_cast<char*>(workspace), ml, st);
-            if (rc) break;
-            POLAR_CUDA(cudaEventRecord(e1, st));
-            POLAR_CUDA(cudaEventSynchronize(e1));
+            cudaError_t e = cudaEventRecord(e0, st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+            int r = mix_bp(codes, ncodes, dcodes, variants, code_of, llr_off, llr, B, max_iters, llr_max, precision,
+                           bits, row_stride, status, iters, static_cast<char*>(workspace), ml, st);
+            if (r) return r;
             float ms = 0;
-            POLAR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep > 0) tmin = std::min(tmin, ms);  // the first run also pays the one-time setup
+            if ((e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+                (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+                return cuda_fail(e, "autotune timing");
+            if (rep > 0) tmin = std::min(tmin, ms);
         }
-        if (rc) break;
-        if (tmin < best) {
-            best = tmin;
-            best_flags = flags;
+        *out = tmin;
+        return POLAR_OK;
+    };
+    // coordinate search: each length in turn keeps the fastest of its options, the others at their
+    // current choice (the lengths share the launch, so each choice is timed on the whole batch)
+    float base = 0.0f, best = 0.0f;
+    rc = time_plans(&base);
+    best = base;
+    for (int n = 7; n <= 11 && !rc; ++n) {
+        if (!present[n]) continue;
+        for (int o = 1; o < nopt[n] && !rc; ++o) {
+            const int keep = pick[n];
+            pick[n] = o;
+            float t = 0.0f;
+            rc = time_plans(&t);
+            if (!rc && t < best) best = t;
+            else pick[n] = keep;
         }
     }
     cudaEventDestroy(e0);
@@ -1183,11 +1257,14 @@ int polar_mixed_autotune(const polar_code* codes, int32_t ncodes, const int32_t*
     if (rc) return rc;
     {
         std::lock_guard<std::mutex> lock(g_mix_mutex);
-        g_mix_variant[precision][8] = (best_flags & 1) ? 2 : 1;
-        g_mix_variant[precision][9] = (best_flags & 2) ? 4 : 3;
+        for (int n = 7; n <= 11; ++n)
+            if (present[n]) g_mix_variant[precision][n] = opts[n][pick[n]];
     }
-    if (chosen) *chosen = best_flags;
+    if (chosen)
+        for (int n = 0; n <= 12; ++n)
+            chosen[n] = (n >= 7 && n <= 11 && present[n]) ? 1 << mix_variant_logr(opts[n][pick[n]]) : 0;
     if (best_ms) *best_ms = best;
+    if (default_ms) *default_ms = base;
     return POLAR_OK;
 }
 
@@ -1213,11 +1290,27 @@ int polar_profile_read(double* bp_ms, int32_t* bp_launches, double* scl_ms, int3
         g_prof.pool.push_back(r.stop);
     }
     g_prof.recs.clear();
+    if (g_prof.err != cudaSuccess && rc == POLAR_OK)
+        rc = cuda_fail(g_prof.err, "event creation or record while profiling (some launches went untimed)");
+    g_prof.err = cudaSuccess;
     if (bp_ms) *bp_ms = t[0];
     if (bp_launches) *bp_launches = cnt[0];
     if (scl_ms) *scl_ms = t[1];
     if (scl_launches) *scl_launches = cnt[1];
     return rc;
+}
+
+int polar_pe_eval(int32_t op, const float* a, const float* b, float* out, int32_t n, void* stream)
+{
+    if (op != POLAR_PE_MINSUM && op != POLAR_PE_EXACT && op != POLAR_PE_EXACT_PACKED)
+        return fail(POLAR_ERR_ARG, "op = %d", op);
+    if (n < 0) return fail(POLAR_ERR_ARG, "n = %d < 0", n);
+    if (n == 0) return POLAR_OK;
+    if (!a || !b || !out) return fail(POLAR_ERR_ARG, "NULL a/b/out");
+    const int threads = 256, work = op == POLAR_PE_EXACT_PACKED ? (n + 1) / 2 : n;
+    pe_eval_kernel<<<(work + threads - 1) / threads, threads, 0, static_cast<cudaStream_t>(stream)>>>(op, a, b, out, n);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? POLAR_OK : cuda_fail(e, "pe_eval_kernel launch");
 }
 
 int polar_hybrid_fallback_count(const void* workspace, int32_t* out, void* stream)

@@ -97,9 +97,11 @@ def polar_transform_bits(x):
 
 def train(code: api.PolarCode, T: int = 20, steps: int = 300, batch: int = 4096, lr: float = 3e-3,
           ebn0_range=(1.0, 4.0), llr_max: float = 20.0, seed: int = 1609093583, log_every: int = 50,
-          w0=None, device="cuda", all_iters: bool = False):
+          w0=None, device="cuda", all_iters: bool = False, w_max: float = 4.0):
     """Adam on the BCE of the information bits of LLR(u) after T iterations (all_iters: the mean
-    of the BCE after every iteration, which rewards early convergence); returns (w, history)."""
+    of the BCE after every iteration, which rewards early convergence), each step followed by a
+    projection of the scales onto [0, w_max]; returns (w, history).  With w_max = 1 the decoders
+    take their unit-scale form (no clip of the scaled term; half2 frame pairs on one iteration)."""
     torch.manual_seed(seed)
     n, N = code.n, code.N
     w = (torch.ones((T, 2, n, N), dtype=torch.float32, device=device) if w0 is None else w0.clone().to(device))
@@ -115,7 +117,7 @@ def train(code: api.PolarCode, T: int = 20, steps: int = 300, batch: int = 4096,
         loss.backward()
         opt.step()
         with torch.no_grad():
-            w.clamp_(0.0, 4.0)
+            w.clamp_(0.0, w_max)
         if step % log_every == 0 or step == steps - 1:
             hist.append((step, float(loss.item())))
     return w.detach(), hist
@@ -191,6 +193,7 @@ def main(argv=None):
     tr.add_argument("--lr", type=float, default=3e-3)
     tr.add_argument("--all-iters", action="store_true", help="loss = mean BCE after every iteration")
     tr.add_argument("--init", type=float, default=1.0, help="initial value of every scale")
+    tr.add_argument("--max-scale", type=float, default=4.0, help="scales are projected onto [0, max-scale]")
     tr.add_argument("--out", required=True)
     ev = sub.add_parser("eval")
     ev.add_argument("--weights", required=True)
@@ -201,9 +204,11 @@ def main(argv=None):
     if a.cmd == "train":
         code = api.make_code(a.N, a.K, a.crc)
         w0 = torch.full((a.T, 2, code.n, code.N), a.init, dtype=torch.float32)
-        w, hist = train(code, T=a.T, steps=a.steps, batch=a.batch, lr=a.lr, w0=w0, all_iters=a.all_iters)
+        w, hist = train(code, T=a.T, steps=a.steps, batch=a.batch, lr=a.lr, w0=w0, all_iters=a.all_iters,
+                        w_max=a.max_scale)
         save(a.out, w, code, a.T, {"steps": a.steps, "batch": a.batch, "lr": a.lr, "ebn0_range": [1.0, 4.0],
-                                   "all_iters": a.all_iters, "init": a.init, "loss_history": hist})
+                                   "all_iters": a.all_iters, "init": a.init, "max_scale": a.max_scale,
+                                   "loss_history": hist})
         print(json.dumps({"saved": a.out, "loss_first": hist[0][1], "loss_last": hist[-1][1]}))
     else:
         w, code, T, _ = load(a.weights)

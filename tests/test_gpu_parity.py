@@ -36,8 +36,8 @@ def run_bp(ocode, llr, max_iters, llr_max, precision=api.POLAR_FP32, w=None, wan
     iters = torch.zeros(B, dtype=torch.int16, device="cuda")
     lu = torch.zeros((B, N), dtype=torch.float32, device="cuda") if want_llr else None
     lx = torch.zeros((B, N), dtype=torch.float32, device="cuda") if want_llr else None
-    api.bp_decode(code, dev(llr), max_iters, llr_max, precision, None if w is None else dev(w), bits, status, iters,
-                  lu, lx)
+    w = None if w is None else (w if isinstance(w, api.PreparedScales) else dev(w))
+    api.bp_decode(code, dev(llr), max_iters, llr_max, precision, w, bits, status, iters, lu, lx)
     torch.cuda.synchronize()
     out = {"bits": api.unpack_bits(bits.cpu().numpy(), ocode.P), "status": status.cpu().numpy(),
            "iters": iters.cpu().numpy().astype(np.int32)}
@@ -137,6 +137,58 @@ def test_hybrid_prepared_weights_reused(precision):
     other = api.POLAR_FP16 if prec == api.POLAR_FP32 else api.POLAR_FP32
     with pytest.raises(api.PolarError):
         dec.hybrid(dev(llr), 12, M, other, pw)
+
+
+@pytest.mark.parametrize("N,K,crc,B", [(128, 64, 8, 203), (256, 128, 16, 97), (512, 256, 16, 45),
+                                     (1024, 512, 16, 37), (2048, 1024, 24, 13)])
+def test_bp_unit_scales_aligned_pairs_bit_exact(N, K, crc, B):
+    """Learned scales within [0, 1] (POLAR_WMS_UNIT) with max_iters <= T: the half2 decoder keeps
+    both frames of a register on the same iteration and skips the clip of the scaled term; every
+    frame still equals the oracle's weighted binary16 BP (bits, status, iterations, LLR(u), LLR(x)),
+    whichever frame shares its register; an odd B leaves one register half empty."""
+    ocode = fr.oracle_code(N, K, crc)
+    code = fr.api_code(ocode)
+    _, llr = fr.frames(ocode, 2.5, B, seed=3100 + N)
+    rng = np.random.default_rng(N + 1)
+    T = 12
+    w = rng.uniform(0.75, 1.0, (T, 2, ocode.n, N)).astype(np.float32)
+    w[0, 0, 0, :4] = 1.0
+    w[1, 1, 0, :4] = 0.0
+    pw = api.PreparedScales(code, dev(w), api.POLAR_FP16)
+    assert pw.unit
+    for imax in (T, 7):
+        ref = oracle.bp_decode(llr, ocode, imax, 32.0, "f16", w=w)
+        assert 0 < np.sum(ref["status"] == api.FRAME_BP_OK) < B
+        got = run_bp(ocode, llr, imax, 32.0, api.POLAR_FP16, w=pw)
+        assert_bp_equal(got, ref, ocode)
+        fixed = run_bp(ocode, llr, imax, 32.0, api.POLAR_FP16 | api.POLAR_FIXED_ITERS, w=pw)
+        assert_bp_equal(fixed, oracle.bp_decode(llr, ocode, imax, 32.0, "f16", early_stop=False, w=w), ocode)
+
+
+@pytest.mark.parametrize("N,K,crc,B,L", [(256, 128, 16, 301, 4), (1024, 512, 16, 150, 8)])
+def test_hybrid_unit_scales_aligned_pairs_bit_exact(N, K, crc, B, L):
+    """The hybrid with learned scales in [0, 1], half2 BP with i_max = T (the aligned-pair form):
+    BP results as the oracle's weighted binary16 BP, CA-SCL on exactly its failures."""
+    ocode = fr.oracle_code(N, K, crc)
+    code = fr.api_code(ocode)
+    _, llr = fr.frames(ocode, 2.5, B, seed=3200 + N)
+    rng = np.random.default_rng(N + 2)
+    T = 10
+    w = rng.uniform(0.75, 1.0, (T, 2, ocode.n, N)).astype(np.float32)
+    pw = api.PreparedScales(code, dev(w), api.POLAR_FP16)
+    ref = oracle.bp_decode(llr, ocode, T, 32.0, "f16", w=w, want_llr=False)
+    u_ref, st_ref = ref["u_hat"].copy(), ref["status"].copy()
+    failed = np.nonzero(st_ref != api.FRAME_BP_OK)[0]
+    assert 0 < len(failed) < B
+    scl = oracle.scl_decode(llr[failed], ocode, L, "f32")
+    u_ref[failed] = scl["u_hat"]
+    st_ref[failed] = scl["status"]
+    dec = api.Decoder(code, B, L)
+    bits, status, iters = dec.hybrid(dev(llr), T, 32.0, api.POLAR_FP16, pw)
+    torch.cuda.synchronize()
+    assert np.array_equal(iters.cpu().numpy().astype(np.int32), ref["iters"])
+    assert np.array_equal(status.cpu().numpy(), st_ref)
+    assert np.array_equal(api.unpack_bits(bits.cpu().numpy(), ocode.P), oracle.payload_of(u_ref, ocode))
 
 
 @pytest.mark.parametrize("N,K,crc,L,frac", [(256, 128, 16, 4, 0.5), (1024, 512, 16, 8, 0.25), (1024, 512, 16, 16, 0.5),
@@ -281,6 +333,51 @@ def test_hybrid_bit_exact(N, K, crc, ebn0, B, imax, L):
     assert np.array_equal(status, ref["status"])
     assert np.array_equal(bits, oracle.payload_of(ref["u_hat"], ocode))
     assert nfb == int(np.sum(ref["status"] != oracle.BP_OK))
+
+
+def _non_finite_frames(ocode, B, seed):
+    """Low-SNR frames (BP often fails) with NaN, +-inf and huge values planted: frame 0 a NaN
+    run, frame 1 infinities of both signs, frame 2 opposite infinities at j and j + N/2 (their
+    top-level g adds inf and -inf), frame 3 a noiseless codeword given as +-inf, the others a few
+    NaN, infinite or huge values."""
+    pay, llr = fr.frames(ocode, 1.5, B, seed=seed)
+    xs = oracle.encode_batch(pay, ocode)
+    N = ocode.N
+    rng = np.random.default_rng(seed)
+    llr[0, 5:40] = np.nan
+    llr[1, ::7] = np.inf
+    llr[1, 3::11] = -np.inf
+    llr[2, 10:20] = np.inf
+    llr[2, N // 2 + 10:N // 2 + 20] = -np.inf
+    pay = np.zeros((1, ocode.P), np.uint8)
+    pay[0, ::3] = 1
+    x = oracle.encode_batch(pay, ocode)[0]
+    llr[3] = np.where(x == 1, -np.inf, np.inf)
+    for b in range(4, B):
+        # NaN, or a huge value or an infinity with the sign of the sent bit
+        pos = np.nonzero(rng.random(N) < 0.03)[0]
+        mag = rng.choice(np.array([np.nan, np.inf, 3e38, 1e31], np.float32), len(pos))
+        llr[b, pos] = np.where(xs[b, pos] == 1, -mag, mag)
+    return llr
+
+
+@pytest.mark.parametrize("N,K,crc,B,L", [(256, 128, 16, 24, 8), (1024, 512, 16, 12, 8), (2048, 1024, 24, 6, 32)])
+def test_scl_and_hybrid_non_finite_inputs(N, K, crc, B, L):
+    """CA-SCL reads NaN as an erasure and saturates +-inf at +-2^100, bit-exactly like the oracle,
+    alone and as the hybrid's fallback for frames whose BP fails."""
+    ocode = fr.oracle_code(N, K, crc)
+    llr = _non_finite_frames(ocode, B, 9100 + N)
+    ref = oracle.scl_decode(llr, ocode, L, "f32")
+    bits, status = run_scl(ocode, llr, L)
+    assert np.array_equal(status, ref["status"])
+    assert np.array_equal(bits, oracle.payload_of(ref["u_hat"], ocode))
+    href = oracle.hybrid_decode(llr, ocode, 30, 20.0, L, precision="f32")
+    assert np.sum(href["status"] != oracle.BP_OK) >= B // 2
+    hbits, hstatus, hiters, nfb = run_hybrid(ocode, llr, 30, L)
+    assert np.array_equal(hiters, href["iters"])
+    assert np.array_equal(hstatus, href["status"])
+    assert np.array_equal(hbits, oracle.payload_of(href["u_hat"], ocode))
+    assert nfb == int(np.sum(href["status"] != oracle.BP_OK))
 
 
 def test_hybrid_full_size_sampled():

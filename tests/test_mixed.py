@@ -83,12 +83,24 @@ def test_mixed_batch_matches_oracle_per_frame(precision):
     assert int(np.sum(ref[1] != oracle.BP_OK)) > 20
     check(ocodes, code_of, dec.bits.cpu().numpy(), dec.status.cpu().numpy(),
           dec.iters.cpu().numpy().astype(np.int32), ref)
-    # the autotuner may switch the plans of N = 256 / 512; results must not change
-    dec.autotune(*args, 40, M, prec)
+    # the autotuner may switch the plans of N = 256 / 512 / 1024; results must not change
+    tuned = dec.autotune(*args, 40, M, prec)
+    assert set(tuned["nodes_per_thread"]) == {oc.N for oc in ocodes}
+    assert tuned["bp_ms"] <= tuned["bp_ms_default_plans"]
     dec.decode(*args, 40, M, prec)
     torch.cuda.synchronize()
     check(ocodes, code_of, dec.bits.cpu().numpy(), dec.status.cpu().numpy(),
           dec.iters.cpu().numpy().astype(np.int32), ref)
+    # every plan of every length, set by hand: the same results
+    for plans in ({256: 4, 512: 4, 1024: 4}, {256: 8, 512: 8, 1024: 8}):
+        for N, npt in plans.items():
+            api.polar_mixed_set_plan(N, npt, prec)
+        dec.decode(*args, 40, M, prec)
+        torch.cuda.synchronize()
+        check(ocodes, code_of, dec.bits.cpu().numpy(), dec.status.cpu().numpy(),
+              dec.iters.cpu().numpy().astype(np.int32), ref)
+    with pytest.raises(api.PolarError):
+        api.polar_mixed_set_plan(2048, 4, prec)
 
 
 def test_mixed_batch_cuda_graph_replay():
