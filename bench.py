@@ -12,6 +12,12 @@ Metric: information (payload) Gbit/s = P x frames / time, summed over all ranks 
 every rank decodes its own frames).  `python bench.py --impl reference` times the CPU oracle on a
 bounded sample of the same workload instead.
 
+Matched FER: outside every timed region, each form (FP32, half2, learned) also decodes
+--stats-ranges further ranges of 100 000 distinct seeded frames (default 10: 10^6 frames); its
+`fer` is taken from those, with a Wilson 95% interval (`fer_ci95`).  `--sweep` runs the default
+workload over Eb/N0 1.0 ... 3.0 dB (one JSON line with a `sweep` list: FER with its interval, BER,
+fallback rate, BP iterations and Gbit/s of each form at each point).
+
 Other workloads (`--workload`, one JSON line each, same keys):
   mixed   2^16 frames per step, N in {128..2048} x R in {1/4, 1/2, 3/4} (CRC-16) drawn per frame
           from a seed, 2.0 dB, i_max 200, L = 8: one persistent BP launch + one CA-SCL launch
@@ -66,6 +72,13 @@ def parse():
     ap.add_argument("--da-bits", type=int, default=128,
                     help="decision-aided block: information positions CA-SCL decides without branching")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_1609_09358_gb300", "weights", "wms_n1024_k512_t20.pt"))
+    ap.add_argument("--stats-ranges", type=int, default=10,
+                    help="ranges of --frames distinct seeded frames each form decodes for its FER (untimed)")
+    ap.add_argument("--sweep", action="store_true", help="default workload swept over --sweep-ebn0")
+    ap.add_argument("--sweep-ebn0", type=float, nargs="+", default=[1.0, 1.5, 2.0, 2.5, 3.0])
+    ap.add_argument("--sweep-ranges", type=int, default=1, help="statistics ranges per sweep point")
+    ap.add_argument("--pipe-rates", action="store_true",
+                    help="measure the issue rates of the instructions behind the BP roofline (one JSON line)")
     return ap.parse_args()
 
 
@@ -226,6 +239,10 @@ def main():
         return run_stress(a, world, rank, local)
     if a.workload == "paper":
         return run_paper(a, world, rank, local)
+    if a.sweep:
+        return run_sweep(a, world, rank, local)
+    if a.pipe_rates:
+        return run_pipe_rates(a, world, rank, local)
 
     import numpy as np
     import torch
@@ -321,11 +338,19 @@ def main():
             f = line.split()
             if len(f) >= 3 and f[0] == "bp_kernel" and f[1] == ("fp16" if prec == api.POLAR_FP16 else "fp32"):
                 traffic = float(f[2])
+    # the survey's count takes g and clip as two operations each (10 per PE half-iteration); on
+    # sm_103a each is one min.xorsign.abs, so the 6-operation count against 128 lanes per SM per
+    # clock is the same bound as the 3 comparisons per PE half-iteration against the comparison
+    # pipe's 64 per SM per clock (half rate), the unit that binds this kernel
+    ops10 = 10 * n * N + K
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Top/s",
                 "frac": achieved / peak_ops, "traffic": traffic, "kernel": "bp_kernel",
                 "ops_per_frame_iter": ops_per_frame_iter, "bp_avg_ms": bp_avg_ms,
-                "peak_basis": "%d SMs x %d lanes x %.0f MHz (sm_max_mhz of MEASURED_PEAKS.json)"
-                              % (sms, lanes, sm_max_mhz)}
+                "peak_basis": "%d SMs x %d lanes x %.0f MHz (sm_max_mhz of MEASURED_PEAKS.json); 6 ops per PE "
+                              "half-iteration = 3 comparison-pipe instructions at half rate" % (sms, lanes, sm_max_mhz),
+                "frac_survey_10op": achieved * ops10 / ops_per_frame_iter / peak_ops,
+                "survey_10op_basis": "10 n N + K ops per frame-iteration (g and clip counted as 2 ops each) "
+                                     "against the same peak"}
 
     line = {"metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -337,6 +362,15 @@ def main():
             "bp_ms_per_step": bp_ms / a.steps, "scl_ms_per_step": scl_ms / a.steps,
             "gpu_launches": bp_n + scl_n, "roofline": roofline, "clocks": clocks}
 
+    # FER of this form over distinct frames beyond the timed batch (untimed)
+    franges = FrameRanges(api, torch, code, B, sigma, dev, rank, world)
+    stats = fer_stats(api, torch, franges, a.stats_ranges,
+                      lambda x: dec.hybrid(x, IMAX, llr_max, prec), dist, dev)
+    if stats:
+        line.update({"fer": stats["fer"], "fer_ci95": stats["fer_ci95"], "ber": stats["ber"],
+                     "fallback_rate": stats["fallback_rate"], "avg_bp_iters": stats["avg_bp_iters"], "stats": stats,
+                     "timed_batch": {"frames": B * world, "fer": fer, "ber": bit_err / (B * P),
+                                     "fallback_rate": n_fb / B, "avg_bp_iters": float(iters.mean())}})
     # Eq. (1): hybrid throughput predicted from the BP and CA-SCL kernels' own throughputs and the
     # BP frame-error (fallback) rate, without launch overhead; against the measured value
     t_bp = P * B / (bp_ms / a.steps * 1e-3) / 1e9
@@ -346,7 +380,7 @@ def main():
     line["eq1"] = {"t_bp_gbit_s": t_bp, "t_scl_gbit_s": t_scl, "gamma_bp_fer": gamma, "theo_gbit_s": theo,
                    "measured_over_theo": value / world / theo}
     if prec == api.POLAR_FP32 and not a.no_learned:
-        line["plain_fp16"] = plain_fp16(a, code, llr, payload, stream, dist)
+        line["plain_fp16"] = plain_fp16(a, code, llr, payload, stream, dist, franges)
         if a.da_bits > 0:
             line["decision_aided"] = decision_aided(a, code, llr, payload, stream, dist)
         if not a.no_variants:
@@ -354,8 +388,8 @@ def main():
             line["reencode_stop"] = bp_variant(a, code, llr, payload, stream, dist, api.POLAR_STOP_REENCODE, 50)
             line["exact_g"] = bp_variant(a, code, llr, payload, stream, dist, api.POLAR_G_EXACT, 5)
     if not a.no_learned and os.path.exists(a.weights):
-        line["learned_fp16"] = learned(a, llr, payload, stream, dist)
-        line["learned_fp16_imax%d" % IMAX] = learned(a, llr, payload, stream, dist, IMAX)
+        line["learned_fp16"] = learned(a, llr, payload, stream, dist, franges=franges)
+        line["learned_fp16_imax%d" % IMAX] = learned(a, llr, payload, stream, dist, IMAX, franges=franges)
     if not a.no_e2e:
         line["e2e"] = e2e(a, code, llr, prec, llr_max, dev, stream, dist)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -449,16 +483,22 @@ def host_scheduled(a, code, llr, payload, stream, dist):
     return {**r, "chunk": 16384, "bp_streams": api.POLAR_SCHED_BP_STREAMS, "dtype": "f32"}
 
 
-def plain_fp16(a, code, llr, payload, stream, dist):
+def plain_fp16(a, code, llr, payload, stream, dist, franges=None):
     """The plain half2 form on the same frames: binary16 BP messages (clip 32), i_max = 200, then
     CA-SCL L = 8 in FP32 on the CRC failures."""
+    import torch
+
     from paper_1609_09358_gb300 import api
     dec = api.Decoder(code, llr.shape[0], LIST, device=llr.device)
     r = _timed_variant(a, code, dec, lambda: dec.hybrid(llr, IMAX, 32.0, api.POLAR_FP16), payload, stream, dist)
-    return {**r, "i_max": IMAX, "dtype": "f16"}
+    r = {**r, "i_max": IMAX, "dtype": "f16"}
+    if franges is not None:
+        _with_stats(r, fer_stats(api, torch, franges, a.stats_ranges,
+                                 lambda x: dec.hybrid(x, IMAX, 32.0, api.POLAR_FP16), dist, llr.device))
+    return r
 
 
-def learned(a, llr, payload, stream, dist, imax=None):
+def learned(a, llr, payload, stream, dist, imax=None, franges=None):
     """The learned/FP16 form on the same frames: half2 BP with the trained per-edge weights,
     T = 20 iterations with CRC early stop, then CA-SCL L = 8 on the CRC failures (imax > T: the
     learned scales in the first T iterations, plain min-sum after them)."""
@@ -495,12 +535,17 @@ def learned(a, llr, payload, stream, dist, imax=None):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     world = dist.get_world_size() if dist else 1
     ferr = (dec.bits != payload).any(dim=1)
-    return {"value": world * lcode.P * B * steps / (float(t.item()) * 1e-3) / 1e9, "unit": "Gbit/s", "steps": steps,
-            "ms_per_step": float(t.item()) / steps, "fer": float(ferr.float().mean().item()),
-            "fallback_rate": float((dec.status != api.FRAME_BP_OK).float().mean().item()),
-            "avg_bp_iters": float(dec.iters.float().mean().item()), "i_max": imax, "learned_iters": T,
-            "bp_ms_per_step": bp_ms / steps, "scl_ms_per_step": scl_ms / steps, "dtype": "f16",
-            "weights": os.path.relpath(a.weights, ROOT), "training": {k: meta.get(k) for k in ("steps", "batch", "lr")}}
+    r = {"value": world * lcode.P * B * steps / (float(t.item()) * 1e-3) / 1e9, "unit": "Gbit/s", "steps": steps,
+         "ms_per_step": float(t.item()) / steps, "fer": float(ferr.float().mean().item()),
+         "fallback_rate": float((dec.status != api.FRAME_BP_OK).float().mean().item()),
+         "avg_bp_iters": float(dec.iters.float().mean().item()), "i_max": imax, "learned_iters": T,
+         "bp_ms_per_step": bp_ms / steps, "scl_ms_per_step": scl_ms / steps, "dtype": "f16",
+         "unit_scales": pw.unit, "weights": os.path.relpath(a.weights, ROOT),
+         "training": {k: meta.get(k) for k in ("steps", "batch", "lr", "all_iters", "max_scale")}}
+    if franges is not None:
+        _with_stats(r, fer_stats(api, torch, franges, a.stats_ranges,
+                                 lambda x: dec.hybrid(x, imax, 32.0, api.POLAR_FP16, pw), dist, llr.device))
+    return r
 
 
 def e2e(a, code, llr, prec, llr_max, dev, stream, dist):
@@ -594,6 +639,177 @@ def _popcount_errors(bits, payload):
     return (diff != 0).any(dim=1), int(lut[diff].sum().item())
 
 
+# ----------------------------------------------------------------------------- FER statistics
+STATS_SEED = SEED + 17          # distinct from the timed batch's frames
+STATS_FRAME0 = 1 << 32          # first frame index of the statistics ranges
+
+
+def wilson_ci(k: int, n: int, z: float = 1.959963984540054):
+    """Wilson score interval (95% for the default z) of a proportion k / n."""
+    import math
+    if n <= 0:
+        return [0.0, 1.0]
+    p = k / n
+    d = 1.0 + z * z / n
+    c = (p + z * z / (2 * n)) / d
+    h = z * math.sqrt(p * (1.0 - p) / n + z * z / (4.0 * n * n)) / d
+    return [max(0.0, c - h), min(1.0, c + h)]
+
+
+class FrameRanges:
+    """Distinct seeded frames of the workload for FER statistics, generated on the device one range
+    of B frames at a time (range r of this rank: frames STATS_FRAME0 + (r world + rank) B ...)."""
+
+    def __init__(self, api, torch, code, B, sigma, dev, rank, world, seed=STATS_SEED):
+        self.api, self.code, self.B, self.sigma, self.rank, self.world, self.seed = api, code, B, sigma, rank, world, seed
+        self.payload = torch.empty((B, code.row_bytes), dtype=torch.uint8, device=dev)
+        self.cw = torch.empty((B, code.N // 8), dtype=torch.uint8, device=dev)
+        self.llr = torch.empty((B, code.N), dtype=torch.float32, device=dev)
+
+    def fill(self, r: int):
+        api, c = self.api, self.code
+        f0 = STATS_FRAME0 + (r * self.world + self.rank) * self.B
+        api.polar_random_payload(self.B, c.P, self.seed, f0, self.payload)
+        api.polar_encode(c, self.payload, self.cw)
+        api.polar_awgn_llr(self.cw, c.N, self.sigma, self.seed, f0, self.llr)
+        return self.llr
+
+
+def fer_stats(api, torch, franges: FrameRanges, nranges: int, decode, dist, dev) -> dict:
+    """Decode `nranges` ranges of distinct frames with decode(llr) -> (bits, status, iters): frame
+    and bit errors, CA-SCL fallbacks and BP iterations summed over the ranges and the ranks."""
+    from paper_1609_09358_gb300 import shard
+    if nranges <= 0:
+        return None
+    fe = be = fb = it = 0
+    for r in range(nranges):
+        bits, status, iters = decode(franges.fill(r))
+        ferr, berr = _popcount_errors(bits, franges.payload)
+        fe += int(ferr.sum().item())
+        be += berr
+        fb += int((status != api.FRAME_BP_OK).sum().item())
+        it += int(iters.long().sum().item())
+    tot = shard.sum_over_ranks({"frames": nranges * franges.B, "fe": fe, "be": be, "fb": fb, "it": it}, dist, dev)
+    n = tot["frames"]
+    return {"frames": n, "frame_errors": tot["fe"], "fer": tot["fe"] / n, "fer_ci95": wilson_ci(tot["fe"], n),
+            "ber": tot["be"] / (n * franges.code.P), "fallback_rate": tot["fb"] / n, "avg_bp_iters": tot["it"] / n,
+            "seed": franges.seed, "first_frame": STATS_FRAME0}
+
+
+def _with_stats(r: dict, st) -> dict:
+    """Replace a form's FER figures (from its timed batch) by those of its statistics pass."""
+    if not st:
+        return r
+    r["timed_batch"] = {k: r.get(k) for k in ("fer", "fallback_rate", "avg_bp_iters")}
+    r.update({"fer": st["fer"], "fer_ci95": st["fer_ci95"], "ber": st["ber"], "fallback_rate": st["fallback_rate"],
+              "avg_bp_iters": st["avg_bp_iters"], "stats": st})
+    return r
+
+
+def run_sweep(a, world, rank, local):
+    """The default workload over Eb/N0: per point, Gbit/s (timed on a batch of --frames frames) and
+    FER with its Wilson interval, BER, fallback rate and BP iterations (--sweep-ranges ranges of
+    distinct frames) of plain FP32, plain half2 and the learned half2 form (i_max = T and 200)."""
+    import numpy as np
+    import torch
+
+    from paper_1609_09358_gb300 import api, build, shard, wms
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    api.load()
+    code = api.make_code(N, K, CRC, 0.0)
+    P, B = code.P, a.frames
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    frame0, _ = shard.frame_range(rank, world, B)
+    payload = torch.empty((B, code.row_bytes), dtype=torch.uint8, device=dev)
+    cw = torch.empty((B, N // 8), dtype=torch.uint8, device=dev)
+    llr = torch.empty((B, N), dtype=torch.float32, device=dev)
+    forms = {"fp32": (IMAX, api.POLAR_FP32, LLR_MAX, None), "fp16": (IMAX, api.POLAR_FP16, 32.0, None)}
+    if os.path.exists(a.weights):
+        w, lcode, T, meta = wms.load(a.weights, device=dev)
+        pw = api.PreparedScales(lcode, w, api.POLAR_FP16)
+        forms["learned_fp16"] = (T, api.POLAR_FP16, 32.0, pw)
+        forms["learned_fp16_imax%d" % IMAX] = (IMAX, api.POLAR_FP16, 32.0, pw)
+    dec = api.Decoder(code, B, LIST, device=dev)
+    steps = max(1, min(a.steps, 10))
+    points, clocks_all = [], []
+    for e in a.sweep_ebn0:
+        sigma = float(np.sqrt(1.0 / (2.0 * (P / N) * 10 ** (e / 10.0))))
+        api.polar_random_payload(B, P, SEED, frame0, payload)
+        api.polar_encode(code, payload, cw)
+        api.polar_awgn_llr(cw, N, sigma, SEED, frame0, llr)
+        franges = FrameRanges(api, torch, code, B, sigma, dev, rank, world)
+        pt = {"ebn0_db": e}
+        for name, (imax, prec, m, pws) in forms.items():
+            def step(imax=imax, prec=prec, m=m, pws=pws):
+                dec.hybrid(llr, imax, m, prec, pws)
+            for _ in range(max(a.warmup, 1)):
+                step()
+            api.polar_profile_enable(True)
+            ms, clk = _timed(step, steps, stream, local, dist)
+            api.polar_profile_enable(False)
+            bp_ms, _, scl_ms, _ = api.polar_profile_read()
+            st = fer_stats(api, torch, franges, a.sweep_ranges, lambda x: dec.hybrid(x, imax, m, prec, pws), dist, dev)
+            pt[name] = {"gbit_s": world * P * B * steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / steps,
+                        "bp_ms_per_step": bp_ms / steps, "scl_ms_per_step": scl_ms / steps, "i_max": imax,
+                        "fer": st["fer"], "fer_ci95": st["fer_ci95"], "frame_errors": st["frame_errors"],
+                        "frames": st["frames"], "ber": st["ber"], "fallback_rate": st["fallback_rate"],
+                        "avg_bp_iters": st["avg_bp_iters"], "clocks": clk}
+            clocks_all.append(clk)
+        points.append(pt)
+    ref = next((p for p in points if abs(p["ebn0_db"] - 2.5) < 1e-9), points[-1])
+    line = {"metric": METRIC, "value": ref["fp32"]["gbit_s"], "unit": "Gbit/s", "n_gpus": world, "steps": steps,
+            "warmup": a.warmup, "ms_per_step": ref["fp32"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Eb/N0 sweep of the plain hybrid N=%d K=%d CRC-16 i_max=%d L=%d, %d frames per "
+                                   "timed step, %d distinct frames per point for the FER" % (N, K, IMAX, LIST, B,
+                                                                                            a.sweep_ranges * B * world),
+                       "ebn0_db": a.sweep_ebn0, "value_point_db": ref["ebn0_db"],
+                       "cache": "inputs larger than L2, no flush"},
+            "sweep": points,
+            "clocks": {"sm_mhz": min((c["sm_mhz"] for c in clocks_all if c.get("sm_mhz")), default=None),
+                       "reasons": sorted({r for c in clocks_all for r in c.get("reasons", [])})}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_pipe_rates(a, world, rank, local):
+    """Issue rates (results of one lane per SM per clock) of the instructions the BP roofline rests on,
+    from the library's microbenchmark (polar_pipe_rate), with the SM clock sampled meanwhile."""
+    import torch
+
+    from paper_1609_09358_gb300 import api, build
+    torch.cuda.set_device(local)
+    build.build()
+    api.load()
+    dev = torch.device("cuda", local)
+    scratch = torch.empty(api.polar_pipe_rate_scratch_bytes(), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    rates = {}
+    for name, op in api.PIPE_RATE_OPS.items():
+        api.polar_pipe_rate(op, 256, scratch)  # warm-up
+        ms, clk = _timed(lambda: rates.__setitem__(name, api.polar_pipe_rate(op, 4096, scratch)), 1, stream,
+                         local, None)
+        rates[name] = {"per_sm_per_clock": rates[name], "ms": ms, "sm_mhz": clk.get("sm_mhz")}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    line = {"metric": "instruction issue rate", "unit": "results of one lane per SM per clock", "n_gpus": 1,
+            "sms": sms, "rates": rates,
+            "method": "32 warps per SM (4 CTAs of 256 threads), 8 independent chains of the instruction per thread, "
+                      "4096 rounds, clock64() around each CTA's loop; rate per SM = instructions of its CTAs / "
+                      "the longest of their cycle counts, averaged over the SMs"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- mixed workload
 MIX_NS = (128, 256, 512, 1024, 2048)
 MIX_RS = (0.25, 0.5, 0.75)
@@ -652,7 +868,8 @@ def run_mixed(a, world, rank, local):
     out = {}
     for name, prec, M in (("fp16", api.POLAR_FP16, 32.0), ("fp32", api.POLAR_FP32, LLR_MAX)):
         dec = api.MixedDecoder(codes, B, MIX_L, device=dev)
-        chosen, _ = dec.autotune(code_of, off, llr, MIX_IMAX, M, prec)
+        tuned = dec.autotune(code_of, off, llr, MIX_IMAX, M, prec)
+        tuned["gain"] = tuned["bp_ms_default_plans"] / tuned["bp_ms"] if tuned["bp_ms"] > 0 else None
         # one profiled eager decode: BP / CA-SCL device time and decoding statistics
         api.polar_profile_enable(True)
         dec.decode(code_of, off, llr, MIX_IMAX, M, prec)
@@ -670,7 +887,7 @@ def run_mixed(a, world, rank, local):
                      "fer": float(ferr.float().mean().item()), "ber": nbit / P_total,
                      "fallback_rate": float((dec.status != api.FRAME_BP_OK).float().mean().item()),
                      "avg_bp_iters": float(iters.mean()), "bp_ms": bp_ms, "scl_ms": scl_ms,
-                     "autotune_variants": chosen, "roofline": _alu_roofline(ops, bp_ms, prec == api.POLAR_FP16, dev),
+                     "autotune": tuned, "roofline": _alu_roofline(ops, bp_ms, prec == api.POLAR_FP16, dev),
                      "clocks": clocks}
         out[name]["roofline"]["kernel"] = "bp_mixed_kernel"
         del dec
@@ -686,7 +903,7 @@ def run_mixed(a, world, rank, local):
             "fer": h["fer"], "ber": h["ber"], "fallback_rate": h["fallback_rate"], "avg_bp_iters": h["avg_bp_iters"],
             "gpu_launches": 5 * steps, "roofline": h["roofline"], "clocks": h["clocks"],
             "fp32": {k: v for k, v in out["fp32"].items() if k != "clocks"},
-            "fp16_detail": {k: h[k] for k in ("bp_ms", "scl_ms", "autotune_variants")}}
+            "fp16_detail": {k: h[k] for k in ("bp_ms", "scl_ms", "autotune")}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -818,6 +1035,11 @@ def run_paper(a, world, rank, local):
     steps = max(1, min(a.steps, 5))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max_mhz = float(_peaks().get("sm_max_mhz", 2070.0))
+    # special-function rates of this GPU (results per SM per clock) for the exact-g roofline
+    scratch = torch.empty(api.polar_pipe_rate_scratch_bytes(), dtype=torch.uint8, device=dev)
+    sf_rates = {k: api.polar_pipe_rate(api.PIPE_RATE_OPS[op], 4096, scratch)
+                for k, op in (("ex2", "ex2.approx.ftz.f32"), ("lg2", "lg2.approx.ftz.f32"))}
+    del scratch
     points, launches = [], 0
     for e in a.paper_ebn0:
         sigma = float(np.sqrt(1.0 / (2.0 * (P / N) * 10 ** (e / 10.0))))
@@ -853,17 +1075,21 @@ def run_paper(a, world, rank, local):
                  "batch_latency_ms": {"mean": float(np.mean(lat)), "max": float(np.max(lat))}, "clocks": clocks}
             if name == "exact_g":
                 # the exact PE function is bound by the special-function units: each g takes two
-                # exponentials (32 per clock per SM on this part) and one logarithm (16 per clock),
-                # i.e. at most 8 g per clock per SM; 2 n N g per frame-iteration
+                # exponentials and one logarithm, so at most 1 / (2 / r_ex2 + 1 / r_lg2) g per
+                # clock per SM with the rates measured on this GPU by the library's
+                # microbenchmark (nominal 32 and 16 per clock: 8 g); 2 n N g per frame-iteration
                 ops = 2.0 * code.n * N * float(it.sum()) * steps
-                peak = sms * 8.0 * sm_max_mhz * 1e6
+                g_clk = 1.0 / (2.0 / sf_rates["ex2"] + 1.0 / sf_rates["lg2"])
+                peak = sms * g_clk * sm_max_mhz * 1e6
                 ach = ops / (bp_ms * 1e-3) if bp_ms > 0 else 0.0
                 r["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
                                  "unit": "T g-evaluations/s", "frac": ach / peak,
                                  "traffic": (lambda t: t * B if t else None)(_exact_traffic_per_frame(N, code.K)),
                                  "kernel": "bp_kernel (exact g)",
-                                 "peak_basis": "%d SMs x 8 g per clock (2 ex2 at 32/clk, 1 lg2 at 16/clk per SM, "
-                                               "measured) x %.0f MHz" % (sms, sm_max_mhz)}
+                                 "peak_basis": "%d SMs x %.2f g per clock (2 ex2 at %.1f/clk, 1 lg2 at %.1f/clk per SM, "
+                                               "measured by polar_pipe_rate in this run; nominal 32 and 16) x %.0f MHz"
+                                               % (sms, g_clk, sf_rates["ex2"], sf_rates["lg2"], sm_max_mhz),
+                                 "frac_of_nominal_8g": ach / (sms * 8.0 * sm_max_mhz * 1e6)}
             else:
                 ops = float((6 * code.n * N + code.K) * it.sum()) * steps
                 r["roofline"] = _alu_roofline(ops, bp_ms, prec == api.POLAR_FP16, dev)
