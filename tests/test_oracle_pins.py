@@ -336,6 +336,32 @@ def test_bp_clip_and_sweep_order_hand_computed(golden_dir, precision):
             assert np.array_equal(out["u_hat"][0], [0 if i in c["frozen"] else int(u[i] < 0) for i in range(N)])
 
 
+@pytest.mark.parametrize("precision", ["f32", "f64", "f16"])
+def test_bp_weighted_update_hand_computed(golden_dir, precision):
+    """The learned variant's update: each g term is scaled by w[t][dir][s-1][output node] before
+    the addition and the clip, iterations past the learned ones run unweighted
+    (tests/golden/bp_weighted_n2.txt, worked out by hand; every value is exact in binary16)."""
+    rows = _read_golden(golden_dir, "bp_weighted_n2.txt")
+    ws, want = {}, []
+    for r in rows:
+        f = r.split()
+        kv = dict(x.split("=") for x in f[2:])
+        if f[0] == "w":
+            ws[int(f[1])] = ([float(v) for v in kv["R"].split(",")], [float(v) for v in kv["L"].split(",")])
+        else:
+            want.append((int(f[1]), [float(v) for v in kv["u"].split(",")], [float(v) for v in kv["x"].split(",")]))
+    T = len(ws)
+    w = np.zeros((T, 2, 1, 2), np.float32)
+    for t, (wr, wl) in ws.items():
+        w[t, 0, 0], w[t, 1, 0] = wr, wl
+    code = _code_from(2, [1])
+    lam = np.array([[15.0, 12.0]], np.float32)
+    for t, u, x in want:
+        out = oracle.bp_decode(lam, code, t, 20.0, precision, early_stop=False, w=w)
+        assert out["llr_u"][0].tolist() == u, (t, out["llr_u"][0])
+        assert out["llr_x"][0].tolist() == x, (t, out["llr_x"][0])
+
+
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_bp_channel_symmetry(precision):
     """Min-sum BP is symmetric: flipping the channel LLRs by a codeword's signs flips every
