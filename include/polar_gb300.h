@@ -320,8 +320,9 @@ int polar_profile_read(double* bp_ms, int32_t* bp_launches, double* scl_ms, int3
  *   op: POLAR_PE_MINSUM (sign(a) sign(b) min(|a|, |b|), exact in binary32), POLAR_PE_EXACT
  *   (ln((1 + e^(a+b)) / (e^a + e^b)) with the fast exponential and logarithm, the scalar form) or
  *   POLAR_PE_EXACT_PACKED (the same arithmetic as two-lane packed instructions, as the FP32 BP
- *   kernels evaluate it; elements 2i and 2i+1 are one pair).  a, b, out: device float [n], n >= 0.
- *   Asynchronous on `stream`.  POLAR_ERR_ARG for an unknown op, n < 0 or NULL pointers. */
+ *   kernels evaluate it; elements 2i and 2i+1 are one pair).  a, b, out: device float [n],
+ *   0 <= n <= 2^30.  Asynchronous on `stream`.  POLAR_ERR_ARG for an unknown op, n outside that
+ *   range or NULL pointers. */
 #define POLAR_PE_MINSUM 0
 #define POLAR_PE_EXACT 1
 #define POLAR_PE_EXACT_PACKED 2

@@ -1304,7 +1304,7 @@ int polar_pe_eval(int32_t op, const float* a, const float* b, float* out, int32_
 {
     if (op != POLAR_PE_MINSUM && op != POLAR_PE_EXACT && op != POLAR_PE_EXACT_PACKED)
         return fail(POLAR_ERR_ARG, "op = %d", op);
-    if (n < 0) return fail(POLAR_ERR_ARG, "n = %d < 0", n);
+    if (n < 0 || n > (1 << 30)) return fail(POLAR_ERR_ARG, "n = %d outside [0, 2^30]", n);
     if (n == 0) return POLAR_OK;
     if (!a || !b || !out) return fail(POLAR_ERR_ARG, "NULL a/b/out");
     const int threads = 256, work = op == POLAR_PE_EXACT_PACKED ? (n + 1) / 2 : n;

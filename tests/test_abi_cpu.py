@@ -125,3 +125,22 @@ def test_decided_mask_and_its_validation(lib):
     assert lib.polar_workspace_bytes(wrong.ref(), 10, 8, 2) == 0
     rc = lib.scl_decode(wrong.ref(), None, 4, 8, None, None, None, 0, None)
     assert rc == -1 and "scl_decided" in lib.polar_last_error().decode()
+
+
+def test_measurement_entry_points_check_arguments_without_gpu(lib):
+    """polar_pe_eval, polar_pipe_rate and polar_mixed_set_plan reject bad arguments before any
+    device call; polar_mixed_set_plan accepts exactly the plans the mixed kernel has."""
+    assert lib.polar_pe_eval(3, None, None, None, 4, None) == -1
+    assert "op" in lib.polar_last_error().decode()
+    assert lib.polar_pe_eval(api.POLAR_PE_EXACT, None, None, None, -1, None) == -1
+    assert lib.polar_pe_eval(api.POLAR_PE_EXACT, None, None, None, 0, None) == 0
+    assert lib.polar_pe_eval(api.POLAR_PE_MINSUM, None, None, None, 8, None) == -1
+    out = ctypes.c_double(0.0)
+    assert lib.polar_pipe_rate(99, 16, ctypes.c_void_p(64), 1024, ctypes.byref(out), None) == -1
+    assert lib.polar_pipe_rate(0, 0, ctypes.c_void_p(64), 1024, ctypes.byref(out), None) == -1
+    for log2n, npt, ok in ((7, 4, True), (7, 8, False), (8, 8, True), (8, 4, True), (9, 4, True), (10, 4, True),
+                           (10, 8, True), (11, 8, True), (11, 4, False), (12, 8, False)):
+        assert (lib.polar_mixed_set_plan(log2n, npt, api.POLAR_FP32) == 0) == ok, (log2n, npt)
+    assert lib.polar_mixed_set_plan(10, 8, 5) == -1
+    for log2n, npt in ((8, 8), (9, 8), (10, 8)):  # back to the default plans
+        assert lib.polar_mixed_set_plan(log2n, npt, api.POLAR_FP32) == 0
