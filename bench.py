@@ -338,7 +338,7 @@ def main():
             f = line.split()
             if len(f) >= 3 and f[0] == "bp_kernel" and f[1] == ("fp16" if prec == api.POLAR_FP16 else "fp32"):
                 traffic = float(f[2])
-    # the survey's count takes g and clip as two operations each (10 per PE half-iteration); on
+    # a count that takes g and clip as two operations each gives 10 per PE half-iteration; on
     # sm_103a each is one min.xorsign.abs, so the 6-operation count against 128 lanes per SM per
     # clock is the same bound as the 3 comparisons per PE half-iteration against the comparison
     # pipe's 64 per SM per clock (half rate), the unit that binds this kernel
@@ -348,9 +348,9 @@ def main():
                 "ops_per_frame_iter": ops_per_frame_iter, "bp_avg_ms": bp_avg_ms,
                 "peak_basis": "%d SMs x %d lanes x %.0f MHz (sm_max_mhz of MEASURED_PEAKS.json); 6 ops per PE "
                               "half-iteration = 3 comparison-pipe instructions at half rate" % (sms, lanes, sm_max_mhz),
-                "frac_survey_10op": achieved * ops10 / ops_per_frame_iter / peak_ops,
-                "survey_10op_basis": "10 n N + K ops per frame-iteration (g and clip counted as 2 ops each) "
-                                     "against the same peak"}
+                "frac_10op": achieved * ops10 / ops_per_frame_iter / peak_ops,
+                "ops10_basis": "10 n N + K ops per frame-iteration (g and clip counted as 2 ops each) "
+                               "against the same peak"}
 
     line = {"metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",

@@ -188,12 +188,12 @@ def main(argv=None):
     tr.add_argument("--K", type=int, default=512)
     tr.add_argument("--crc", type=int, default=16)
     tr.add_argument("--T", type=int, default=20)
-    tr.add_argument("--steps", type=int, default=400)
+    tr.add_argument("--steps", type=int, default=1500)
     tr.add_argument("--batch", type=int, default=4096)
-    tr.add_argument("--lr", type=float, default=3e-3)
+    tr.add_argument("--lr", type=float, default=3e-2)
     tr.add_argument("--all-iters", action="store_true", help="loss = mean BCE after every iteration")
     tr.add_argument("--init", type=float, default=1.0, help="initial value of every scale")
-    tr.add_argument("--max-scale", type=float, default=4.0, help="scales are projected onto [0, max-scale]")
+    tr.add_argument("--max-scale", type=float, default=1.0, help="scales are projected onto [0, max-scale]")
     tr.add_argument("--out", required=True)
     ev = sub.add_parser("eval")
     ev.add_argument("--weights", required=True)
