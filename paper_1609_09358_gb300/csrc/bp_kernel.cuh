@@ -372,17 +372,19 @@ __device__ __forceinline__ WRow<E, R> wms_ones()
 
 template <int LOGN>
 struct BPConfig;  // thread plan and frames (or frame pairs) per CTA for each block length
-// MIN_CTAS / MIN_CTAS_W: resident CTAs per SM the register allocation of the plain / weighted
-// kernel must allow (launch bounds)
-template <> struct BPConfig<7>  { using Plan = BPPlan<7, 2>;  static constexpr int F = 4, MIN_CTAS = 4, MIN_CTAS_W = 4; };
-template <> struct BPConfig<8>  { using Plan = BPPlan<8, 3>;  static constexpr int F = 4, MIN_CTAS = 4, MIN_CTAS_W = 3; };
-template <> struct BPConfig<9>  { using Plan = BPPlan<9, 3>;  static constexpr int F = 1, MIN_CTAS = 8, MIN_CTAS_W = 5; };
-template <> struct BPConfig<10> { using Plan = BPPlan<10, 3>; static constexpr int F = 1, MIN_CTAS = 4, MIN_CTAS_W = 3; };
-template <> struct BPConfig<11> { using Plan = BPPlan<11, 3>; static constexpr int F = 1, MIN_CTAS = 2, MIN_CTAS_W = 1; };
+// MIN_CTAS / MIN_CTAS_W / MIN_CTAS_U: resident CTAs per SM the register allocation of the plain /
+// weighted / unit-scale weighted kernel must allow (launch bounds).  The unit-scale kernel at
+// N = 2048 takes 2 CTAs (128 registers, 68 bytes of spill): 15% faster than 1 CTA at 171
+// registers; at N = 1024 4 CTAs measured no faster than 3.
+template <> struct BPConfig<7>  { using Plan = BPPlan<7, 2>;  static constexpr int F = 4, MIN_CTAS = 4, MIN_CTAS_W = 4, MIN_CTAS_U = 4; };
+template <> struct BPConfig<8>  { using Plan = BPPlan<8, 3>;  static constexpr int F = 4, MIN_CTAS = 4, MIN_CTAS_W = 3, MIN_CTAS_U = 3; };
+template <> struct BPConfig<9>  { using Plan = BPPlan<9, 3>;  static constexpr int F = 1, MIN_CTAS = 8, MIN_CTAS_W = 5, MIN_CTAS_U = 5; };
+template <> struct BPConfig<10> { using Plan = BPPlan<10, 3>; static constexpr int F = 1, MIN_CTAS = 4, MIN_CTAS_W = 3, MIN_CTAS_U = 3; };
+template <> struct BPConfig<11> { using Plan = BPPlan<11, 3>; static constexpr int F = 1, MIN_CTAS = 2, MIN_CTAS_W = 1, MIN_CTAS_U = 2; };
 // N = 4096: one frame group of 512 threads per SM; the live messages of a thread (about n + 1
 // columns of 8 nodes: the R columns the coming L sweep reads and the L columns the coming R sweep
 // reads) fit its 128 registers, so the frame stays on one SM without a cluster
-template <> struct BPConfig<12> { using Plan = BPPlan<12, 3>; static constexpr int F = 1, MIN_CTAS = 1, MIN_CTAS_W = 1; };
+template <> struct BPConfig<12> { using Plan = BPPlan<12, 3>; static constexpr int F = 1, MIN_CTAS = 1, MIN_CTAS_W = 1, MIN_CTAS_U = 1; };
 
 template <class P>
 __host__ __device__ constexpr int bp_slot_words()
@@ -888,6 +890,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 template <int LOGN, int WEIGHTED, int VAR>
 constexpr int bp_min_ctas()
 {
+    if (WEIGHTED == 2) return BPConfig<LOGN>::MIN_CTAS_U;
     return WEIGHTED != 0 || ((VAR & 1) && LOGN <= 10) ? BPConfig<LOGN>::MIN_CTAS_W : BPConfig<LOGN>::MIN_CTAS;
 }
 
