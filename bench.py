@@ -379,6 +379,8 @@ def main():
     theo = t_bp * t_scl / (t_scl + gamma * t_bp) if t_scl else t_bp
     line["eq1"] = {"t_bp_gbit_s": t_bp, "t_scl_gbit_s": t_scl, "gamma_bp_fer": gamma, "theo_gbit_s": theo,
                    "measured_over_theo": value / world / theo}
+    line["two_in_flight"] = two_in_flight(api, torch, code, llr, IMAX, llr_max, prec, None, max(1, min(a.steps, 30)),
+                                          dist)
     if prec == api.POLAR_FP32 and not a.no_learned:
         line["plain_fp16"] = plain_fp16(a, code, llr, payload, stream, dist, franges)
         if a.da_bits > 0:
@@ -495,6 +497,8 @@ def plain_fp16(a, code, llr, payload, stream, dist, franges=None):
     if franges is not None:
         _with_stats(r, fer_stats(api, torch, franges, a.stats_ranges,
                                  lambda x: dec.hybrid(x, IMAX, 32.0, api.POLAR_FP16), dist, llr.device))
+    r["two_in_flight"] = two_in_flight(api, torch, code, llr, IMAX, 32.0, api.POLAR_FP16, None,
+                                       max(1, min(a.steps, 30)), dist)
     return r
 
 
@@ -545,6 +549,8 @@ def learned(a, llr, payload, stream, dist, imax=None, franges=None):
     if franges is not None:
         _with_stats(r, fer_stats(api, torch, franges, a.stats_ranges,
                                  lambda x: dec.hybrid(x, imax, 32.0, api.POLAR_FP16, pw), dist, llr.device))
+    r["two_in_flight"] = two_in_flight(api, torch, lcode, llr, imax, 32.0, api.POLAR_FP16, pw,
+                                       max(1, min(a.steps, 30)), dist)
     return r
 
 
@@ -637,6 +643,46 @@ def _popcount_errors(bits, payload):
     lut = torch.tensor([bin(v).count("1") for v in range(256)], dtype=torch.int64, device=bits.device)
     diff = (bits ^ payload).long()
     return (diff != 0).any(dim=1), int(lut[diff].sum().item())
+
+
+def two_in_flight(api, torch, code, llr, imax, llr_max, prec, pws, steps, dist, n=2):
+    """The same hybrid steps with n batches in flight: step i runs on stream i mod n with its own
+    decoder, so the CA-SCL launch of one batch overlaps the BP launch of the next, as in the paper's
+    concurrent BP / SCL scheduling (Fig. 3) and in a receiver that decodes a stream of batches."""
+    B = llr.shape[0]
+    decs = [api.Decoder(code, B, LIST, device=llr.device) for _ in range(n)]
+    streams = [torch.cuda.Stream(device=llr.device) for _ in range(n)]
+    main = torch.cuda.current_stream()
+
+    def run(k):
+        ev = torch.cuda.Event()
+        ev.record(main)
+        for s in streams:
+            s.wait_event(ev)
+        for i in range(k):
+            d, s = decs[i % n], streams[i % n]
+            api.hybrid_decode(code, llr, imax, llr_max, prec, pws, LIST, d.bits, d.status, d.iters, d.workspace, s)
+        for s in streams:
+            e = torch.cuda.Event()
+            e.record(s)
+            main.wait_event(e)
+
+    run(2 * n)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(main)
+    run(steps)
+    e1.record(main)
+    torch.cuda.synchronize()
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=llr.device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    world = dist.get_world_size() if dist else 1
+    ms = float(t.item())
+    return {"value": world * code.P * B * steps / (ms * 1e-3) / 1e9, "unit": "Gbit/s", "ms_per_step": ms / steps,
+            "steps": steps, "batches_in_flight": n}
 
 
 # ----------------------------------------------------------------------------- FER statistics
