@@ -402,6 +402,49 @@ def test_hybrid_full_size_sampled():
     assert np.all(iters[ok] >= 1) and np.all(iters[~ok] == 200)
 
 
+@pytest.mark.parametrize("form", ["half2", "learned"])
+def test_half2_and_learned_full_size_sampled(form):
+    """The default workload's half2 forms as the benchmark launches them (N = 1024, K = 512, 1e5
+    frames, 2.5 dB, L = 8): plain half2 BP with i_max = 200, and the learned form with the shipped
+    scales (all in [0, 1]) and i_max = T = 20, i.e. the aligned-pair kernel.  Every status is valid;
+    a random sample plus CA-SCL frames equal the oracle's binary16 (weighted) BP followed by its
+    CA-SCL, frame by frame."""
+    import os
+    from paper_1609_09358_gb300 import wms
+    ocode = fr.oracle_code(1024, 512, 16)
+    code = fr.api_code(ocode)
+    B = 100_000
+    _, llr = fr.frames_large(ocode, 2.5, B, seed=1609093586)
+    w_np, pw, imax = None, None, 200
+    if form == "learned":
+        wfile = os.path.join(os.path.dirname(api.__file__), "weights", "wms_n1024_k512_t20.pt")
+        w, wcode, imax, _ = wms.load(wfile, device="cuda")
+        assert np.array_equal(wcode.frozen, ocode.frozen)
+        pw = api.PreparedScales(code, w, api.POLAR_FP16)
+        assert pw.unit
+        w_np = w.cpu().numpy()
+    dec = api.Decoder(code, B, L=8)
+    dec.hybrid(torch.from_numpy(llr).cuda(), imax, 32.0, api.POLAR_FP16, pw)
+    torch.cuda.synchronize()
+    status = dec.status.cpu().numpy()
+    iters = dec.iters.cpu().numpy().astype(np.int32)
+    assert set(np.unique(status)) <= {1, 2, 3}
+    rng = np.random.default_rng(11)
+    fb = np.nonzero(status != oracle.BP_OK)[0]
+    sample = np.unique(np.concatenate([rng.choice(B, 150, replace=False), fb[:100]]))
+    rows = llr[sample]
+    bp = oracle.bp_decode(rows, ocode, imax, 32.0, "f16", w=w_np, want_llr=False)
+    u, st = bp["u_hat"].copy(), bp["status"].copy()
+    failed = st != oracle.BP_OK
+    if failed.any():
+        scl = oracle.scl_decode(rows[failed], ocode, 8, "f32")
+        u[failed], st[failed] = scl["u_hat"], scl["status"]
+    assert np.array_equal(iters[sample], bp["iters"])
+    assert np.array_equal(status[sample], st)
+    assert np.array_equal(api.unpack_bits(dec.bits.cpu().numpy()[sample], ocode.P), oracle.payload_of(u, ocode))
+    assert np.all(iters[status == oracle.BP_OK] >= 1) and np.all(iters[status != oracle.BP_OK] == imax)
+
+
 def test_encoder_bit_exact():
     for N, K, crc in [(128, 64, 8), (256, 100, 16), (1024, 512, 16), (2048, 1024, 24), (512, 24, 24), (4096, 2048, 16)]:
         ocode = fr.oracle_code(N, K, crc, design_rate=K / N)
