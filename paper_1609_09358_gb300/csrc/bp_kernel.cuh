@@ -396,7 +396,8 @@ __host__ __device__ constexpr int bp_slot_words()
 
 // One frame group of T threads decoding frames from `src` until it runs dry.  Group `slot` of
 // the CTA uses the shared-memory slice `slot_smem` (bp_slot_words<P>() words).
-// SYNP (half2 only): both frames' CRC syndromes in one word -- for CRCs of at most 16 bits.
+// SYNP (CRCs of at most 16 bits): half2 keeps both frames' CRC syndromes in one word; FP32 with
+// the PE pairs keeps the syndrome columns of two adjacent nodes in one word.
 // VAR (FP32, unweighted): bit 0 the exact PE function instead of min-sum, bit 1 the re-encoding
 // stop -- the frame stops at the first iteration where HD(LLR(x)) equals the re-encoded HD(LLR(u))
 // (x = u G, Sec. II-B) and counts as decoded iff its CRC then holds.
@@ -491,15 +492,23 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 
     MSG Lc[n + 2][R];
     MSG Rc[n + 2][R];
-    // SYNP: both frames' syndromes share one word (frame 0 in the low half, frame 1 in the high
-    // half), the columns are stored doubled
-    static_assert(!SYNP || FPT == 2, "packed syndromes are for half2 messages");
+    // SYNP, half2: both frames' syndromes share one word (frame 0 in the low half, frame 1 in the
+    // high half), the columns are stored doubled.  SYNP, FP32 pairs: registers k and k + 1 share
+    // one column word (k's column low, k + 1's high), two such words per thread and uint2,
+    // [R/4][T]; the accumulated word's halves XOR to the syndrome.
+    static_assert(!SYNP || FPT == 2 || (PAIRS && R % 4 == 0), "packed syndromes: half2, or FP32 pairs");
     constexpr bool syn_packed = SYNP;
+    constexpr bool syn_nodes = SYNP && FPT == 1;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const int j = P::node(0, t, k);
         const uint32_t col = C.colsyn[j];
-        csyn[k * T + t] = syn_packed ? (col | (col << 16)) : col;
+        if constexpr (syn_nodes) {
+            if (!(k & 1))
+                csyn[(k >> 2) * 2 * T + 2 * t + ((k >> 1) & 1)] = col | (C.colsyn[P::node(0, t, k + 1)] << 16);
+        } else {
+            csyn[k * T + t] = syn_packed ? (col | (col << 16)) : col;
+        }
         Rc[1][k] = frozen_at(C.frozen_bits, j) ? Mv : MT::splat(0.0f);
     }
     {
@@ -755,7 +764,24 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                 // information nodes decided 1 (frozen nodes have column 0).  On an information
                 // node R[1] = +0, so u is never -0 and its sign bit is exactly (u < 0): the
                 // decision is an arithmetic shift and the update one and-xor.
-                if constexpr (syn_packed) {
+                if constexpr (syn_nodes) {
+                    // one byte permute replicates the sign bits of u[k] and u[k + 1] into a 16|16
+                    // mask over the pair's column word; one 64-bit load brings two such words
+                    const uint2* cs2 = reinterpret_cast<const uint2*>(csyn);
+#pragma unroll
+                    for (int k = 0; k < R; k += 4) {
+                        const uint2 cw = cs2[(k >> 2) * T + t];
+                        const float2 u0 = __fadd2_rn(make_float2(Lc[1][k], Lc[1][k + 1]),
+                                                     make_float2(Rc[1][k], Rc[1][k + 1]));
+                        const float2 u1 = __fadd2_rn(make_float2(Lc[1][k + 2], Lc[1][k + 3]),
+                                                     make_float2(Rc[1][k + 2], Rc[1][k + 3]));
+                        uint32_t m0, m1;
+                        asm("prmt.b32 %0, %1, %2, 0xFFBB;" : "=r"(m0) : "r"(__float_as_uint(u0.x)), "r"(__float_as_uint(u0.y)));
+                        asm("prmt.b32 %0, %1, %2, 0xFFBB;" : "=r"(m1) : "r"(__float_as_uint(u1.x)), "r"(__float_as_uint(u1.y)));
+                        syn0 ^= cw.x & m0;
+                        syn0 ^= cw.y & m1;
+                    }
+                } else if constexpr (syn_packed) {
                     // one byte permute replicates the sign bits of both halves into a 16|16 mask
 #pragma unroll
                     for (int k = 0; k < R; ++k) {
@@ -808,7 +834,9 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
                 if constexpr (FPT == 2 && !syn_packed) syn1 ^= sp[NW + w];
             }
         }
-        if constexpr (syn_packed) {
+        if constexpr (syn_nodes) {
+            syn0 = (syn0 ^ (syn0 >> 16)) & 0xFFFFu;
+        } else if constexpr (syn_packed) {
             syn1 = syn0 >> 16;
             syn0 &= 0xFFFFu;
         }

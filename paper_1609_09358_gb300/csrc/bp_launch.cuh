@@ -15,9 +15,10 @@ struct BPKernelInfo {
 
 // kernel of (log2 N, weighted) for the message type of this translation unit (weighted: 0 plain,
 // 1 learned scales, 2 learned scales within [-1, 1] with both frames of a half2 register on the
-// same iteration -- FP32 takes the form-1 kernel for 2); half2 plain kernels come in a variant
-// with both frames' CRC syndromes in one word (crc_len <= 16)
-BPKernelInfo bp_kernel_info_fp32(int logn, int weighted);
+// same iteration -- FP32 takes the form-1 kernel for 2); plain kernels come in a variant for
+// crc_len <= 16 that packs the CRC syndrome into 16-bit halves (half2: both frames' syndromes in
+// one word; FP32: the columns of two nodes in one word)
+BPKernelInfo bp_kernel_info_fp32(int logn, int weighted, bool packed_syndrome);
 // FP32 unweighted kernel of a BP variant: bit 0 exact PE function, bit 1 re-encoding stop
 BPKernelInfo bp_kernel_info_fp32_var(int logn, int var);
 BPKernelInfo bp_kernel_info_fp16(int logn, int weighted, bool packed_syndrome);
@@ -67,11 +68,8 @@ BPKernelInfo bp_kernel_info_t(int logn, int weighted, bool packed_syndrome = fal
             else
                 return BPKernelInfo{(const void*)bp_kernel<LOGN, MSG, 1, TH>, TH, smem, Cfg::F};
         }
-        if constexpr (std::is_same<MSG, __half2>::value)
-            fn = packed_syndrome ? (const void*)bp_kernel<LOGN, MSG, 0, TH, true>
-                                 : (const void*)bp_kernel<LOGN, MSG, 0, TH>;
-        else
-            fn = (const void*)bp_kernel<LOGN, MSG, 0, TH>;
+        fn = packed_syndrome ? (const void*)bp_kernel<LOGN, MSG, 0, TH, true>
+                             : (const void*)bp_kernel<LOGN, MSG, 0, TH>;
         return {fn, TH, smem, Cfg::F};
     };
     switch (logn) {

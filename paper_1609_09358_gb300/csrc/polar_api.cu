@@ -381,7 +381,7 @@ static int launch_bp(const DevCode* dcode, const polar_code* code, const float* 
     const int weighted = !w ? 0 : (unit && precision == POLAR_FP16 && max_iters <= w_iters) ? 2 : 1;
     const BPKernelInfo k = precision == POLAR_FP16 ? bp_kernel_info_fp16(n, weighted, code->crc_len <= 16)
                            : var               ? bp_kernel_info_fp32_var(n, var)
-                                               : bp_kernel_info_fp32(n, weighted);
+                                               : bp_kernel_info_fp32(n, weighted, code->crc_len <= 16);
     if (!k.fn) return fail(POLAR_ERR_ARG, "no BP kernel for N = %d with these options", code->N);
     if (k.smem > 48 * 1024) {
         // above the default dynamic shared-memory limit (N = 4096); set once per kernel and device

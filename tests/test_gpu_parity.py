@@ -65,6 +65,7 @@ BP_CASES = [
     (1024, 512, 16, 2.5, 37, 200),
     (1024, 512, 16, 1.0, 12, 200),
     (2048, 1024, 24, 1.5, 9, 80),
+    (1024, 512, 24, 2.0, 19, 100),   # CRC-24: the syndrome columns unpacked
     (1024, 768, 16, 3.0, 21, 100),
     (256, 64, 16, 1.0, 33, 40),
     (4096, 2048, 16, 2.0, 7, 50),    # the paper's length: one 512-thread frame group per SM
