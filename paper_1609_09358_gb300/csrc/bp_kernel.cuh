@@ -520,13 +520,12 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             Lc[n + 1][k] = MT::pair(y0 ? stage_clip(__ldg(y0 + j), M) : 0.0f, y1 ? stage_clip(__ldg(y1 + j), M) : 0.0f);
         }
     }
+    // messages start at 0; only the L columns 2..n need it, since every R sweep writes R[2..n]
+    // before anything reads them
 #pragma unroll
     for (int c = 2; c <= n; ++c)
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
-            Lc[c][k] = MT::splat(0.0f);
-            Rc[c][k] = MT::splat(0.0f);
-        }
+        for (int k = 0; k < R; ++k) Lc[c][k] = MT::splat(0.0f);
 
     // Learned scales: iteration `it` of half h reads its prepared rows; past the learned
     // iterations (and for an idle half) the scale is 1, the same value as the plain update since
@@ -625,7 +624,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
         }
     };
 
-    // replace the frame of half h by the next one: channel column and zeroed messages
+    // replace the frame of half h by the next one: channel column and zeroed L messages (the R
+    // columns are rewritten by the next R sweep before they are read)
     auto refill = [&](int h) {
         fr[h] = fetch();
         itc[h] = 0;
@@ -638,10 +638,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 #pragma unroll
         for (int c = 2; c <= n; ++c)
 #pragma unroll
-            for (int k = 0; k < R; ++k) {
-                Lc[c][k] = MT::zero_half(Lc[c][k], h);
-                Rc[c][k] = MT::zero_half(Rc[c][k], h);
-            }
+            for (int k = 0; k < R; ++k) Lc[c][k] = MT::zero_half(Lc[c][k], h);
     };
 
     int it = 0;  // iterations run by this group (selects the partial-syndrome slot parity)
