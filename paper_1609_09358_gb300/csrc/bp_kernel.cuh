@@ -52,13 +52,16 @@ struct BPPlan {
     // 1, 2, 4, 8, 16 modulo 32 in some order -- for group 1 that takes node bits 0, 1, 2, 8, 9
     // (a search over the plans finds such bits for N >= 1024 with b = 3 only).  The other plans
     // keep an XOR swizzle of index bits 5..7 into the bank bits (one XOR per access).
-    static constexpr bool PAD = LOGR == 3 && LOGN >= 10;
+    static constexpr bool PAD = (LOGR == 3 && LOGN >= 10) || (LOGR == 4 && LOGN == 10);
     // node bit receiving thread-index bit q in group g: the non-window bits in ascending order,
-    // except that group 1 of a PAD plan puts lane bits 3, 4 on node bits 8, 9
+    // except that group 1 of a PAD plan puts lane bits 3, 4 on node bits 8, 9 (b = 3) or lane
+    // bit 4 on node bit 9 (b = 4, N = 1024)
     __host__ __device__ static constexpr int tbit(int g, int q)
     {
-        if (PAD && g == 1)  // window 3..5: thread bits -> node bits 0 1 2 8 9 6 7 10 ...
+        if (PAD && LOGR == 3 && g == 1)  // window 3..5: thread bits -> node bits 0 1 2 8 9 6 7 10 ...
             return q < 3 ? q : q < 5 ? q + 5 : q < 7 ? q + 1 : q + 3;
+        if (PAD && LOGR == 4 && g == 1)  // window 4..7: thread bits -> node bits 0 1 2 3 9 8
+            return q < 4 ? q : q == 4 ? 9 : 8;
         return q < win(g) ? q : q + LOGR;
     }
     // node bits from the thread index t (group g) and from the register index k
@@ -385,6 +388,20 @@ template <> struct BPConfig<11> { using Plan = BPPlan<11, 3>; static constexpr i
 // columns of 8 nodes: the R columns the coming L sweep reads and the L columns the coming R sweep
 // reads) fit its 128 registers, so the frame stays on one SM without a cluster
 template <> struct BPConfig<12> { using Plan = BPPlan<12, 3>; static constexpr int F = 1, MIN_CTAS = 1, MIN_CTAS_W = 1, MIN_CTAS_U = 1; };
+
+// Plan and frame groups per CTA of a kernel: the plain min-sum kernels at N = 1024 take 16 nodes
+// per thread (64 threads per frame, 4 column exchanges per iteration instead of 6), the others
+// the length's plan.
+template <int LOGN, int WEIGHTED, int VAR>
+struct BPKernelPlan {
+    using Plan = typename BPConfig<LOGN>::Plan;
+    static constexpr int F = BPConfig<LOGN>::F;
+};
+template <>
+struct BPKernelPlan<10, 0, 0> {
+    using Plan = BPPlan<10, 4>;
+    static constexpr int F = 1;
+};
 
 template <class P>
 __host__ __device__ constexpr int bp_slot_words()
@@ -924,8 +941,8 @@ constexpr int bp_min_ctas()
 template <int LOGN, class MSG, int WEIGHTED, int THREADS, bool SYNP = false, int VAR = 0>
 __global__ void __launch_bounds__(THREADS, bp_min_ctas<LOGN, WEIGHTED, VAR>()) bp_kernel(const BPArgs a)
 {
-    using P = typename BPConfig<LOGN>::Plan;
-    constexpr int F = BPConfig<LOGN>::F;
+    using P = typename BPKernelPlan<LOGN, WEIGHTED, VAR>::Plan;
+    constexpr int F = BPKernelPlan<LOGN, WEIGHTED, VAR>::F;
     static_assert(THREADS == F * P::T, "launch shape");
     static_assert(P::T <= 32 || F == 1, "frame groups wider than a warp own their CTA");
     extern __shared__ uint32_t smem[];

@@ -57,6 +57,11 @@ BPKernelInfo bp_kernel_info_t(int logn, int weighted, bool packed_syndrome = fal
         constexpr int TH = Cfg::F * P::T;
         const size_t smem = (size_t)Cfg::F * bp_slot_words<P>() * 4;
         const void* fn;
+        // the plain kernels' own plan
+        using KP = BPKernelPlan<LOGN, 0, 0>;
+        using P0 = typename KP::Plan;
+        constexpr int TH0 = KP::F * P0::T;
+        const size_t smem0 = (size_t)KP::F * bp_slot_words<P0>() * 4;
         if (weighted) {
             // learned weights: N <= 2048 (no weighted kernel is built for longer codes)
             if constexpr (LOGN > 11)
@@ -68,9 +73,9 @@ BPKernelInfo bp_kernel_info_t(int logn, int weighted, bool packed_syndrome = fal
             else
                 return BPKernelInfo{(const void*)bp_kernel<LOGN, MSG, 1, TH>, TH, smem, Cfg::F};
         }
-        fn = packed_syndrome ? (const void*)bp_kernel<LOGN, MSG, 0, TH, true>
-                             : (const void*)bp_kernel<LOGN, MSG, 0, TH>;
-        return {fn, TH, smem, Cfg::F};
+        fn = packed_syndrome ? (const void*)bp_kernel<LOGN, MSG, 0, TH0, true>
+                             : (const void*)bp_kernel<LOGN, MSG, 0, TH0>;
+        return {fn, TH0, smem0, KP::F};
     };
     switch (logn) {
         case 7: return pick(std::integral_constant<int, 7>{});
