@@ -389,6 +389,15 @@ template <> struct BPConfig<11> { using Plan = BPPlan<11, 3>; static constexpr i
 // reads) fit its 128 registers, so the frame stays on one SM without a cluster
 template <> struct BPConfig<12> { using Plan = BPPlan<12, 3>; static constexpr int F = 1, MIN_CTAS = 1, MIN_CTAS_W = 1, MIN_CTAS_U = 1; };
 
+// first R-sweep stage whose outputs cross into another group (0: none)
+template <class P>
+__host__ __device__ constexpr int first_rcross()
+{
+    for (int s = 1; s <= P::LOGN; ++s)
+        if (P::rcross(s)) return s;
+    return 0;
+}
+
 // Plan and frame groups per CTA of a kernel: the plain min-sum kernels at N = 1024 take 16 nodes
 // per thread (64 threads per frame, 4 column exchanges per iteration instead of 6), the others
 // the length's plan.
@@ -658,6 +667,16 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             for (int k = 0; k < R; ++k) Lc[c][k] = MT::zero_half(Lc[c][k], h);
     };
 
+    // DEFER (one FP32 frame over several warps): the warps' partial syndromes of an iteration are
+    // read after the first exchange barrier of the next one, which orders them, instead of after
+    // a barrier of their own.  The next iteration's stages before that barrier are computed
+    // before the stop decision; if the frame stops they are dropped.  They write only R[2..SC]
+    // and the exchange buffer, and the outputs read L[1], R[1], R[n] and L[n+1] (SC < n).
+    constexpr int SC = first_rcross<P>();
+    // (Not in the mixed kernel, whose many plans would spill more with it.)
+    constexpr bool DEFER = FPT == 1 && !WEIGHTED && !REENC && NW > 1 && SC > 0 && SC < n &&
+                           std::is_same<Src, CounterSource>::value;
+    bool pending = false;  // DEFER: an iteration's partial syndromes are written, not yet read
     int it = 0;  // iterations run by this group (selects the partial-syndrome slot parity)
     for (;;) {
         // scales of the stage being computed and of the next one (loaded a stage ahead)
@@ -665,7 +684,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
         if constexpr (WEIGHTED) wc = wload(0, 1);
         uint32_t xh = 0;  // re-encoding stop: HD(LLR(x)) of this thread's channel-column nodes
         // ------------------------------------------------------------------ R sweep
-        static_for<1, n + 1>([&](auto S) {
+        auto rstage = [&](auto S) {
             constexpr int s = S.value, q = s - 1, g = P::grp(q), dd = 1 << (q - P::win(g));
             constexpr bool last = s == n;
             constexpr bool cross = P::rcross(s);
@@ -718,11 +737,37 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             }
             if constexpr (cross) {
                 group_sync<T, SHARED_CTA>(slot);
+                if constexpr (!(DEFER && s == SC)) {
 #pragma unroll
-                for (int k = 0; k < R; ++k) Rc[s + 1][k] = xget<P, P::grp(s)>(xb, xbase, t, k);
+                    for (int k = 0; k < R; ++k) Rc[s + 1][k] = xget<P, P::grp(s)>(xb, xbase, t, k);
+                }
             }
             if constexpr (WEIGHTED) wc = wn;
-        });
+        };
+        if constexpr (DEFER) {
+            static_for<1, SC + 1>(rstage);
+            if (pending) {
+                // the previous iteration's stop decision, from its partial syndromes
+                pending = false;
+                const uint32_t* sp = synp + ((it - 1) & 1) * 2 * NW;
+                uint32_t sy = 0;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) sy ^= sp[w];
+                if constexpr (syn_nodes) sy = (sy ^ (sy >> 16)) & 0xFFFFu;
+                const bool ok = sy == 0u;
+                if ((ok && !a.fixed_iters) || itc[0] >= a.max_iters) {
+                    finalize(0, itc[0], ok);
+                    refill(0);
+                    if (fr[0] < 0) break;
+                    continue;  // the new frame starts its first R sweep
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < R; ++k) Rc[SC + 1][k] = xget<P, P::grp(SC)>(xbuf + (P::xidx_r(SC) & 1) * P::XW, xbase, t, k);
+            static_for<SC + 1, n + 1>(rstage);
+        } else {
+            static_for<1, n + 1>(rstage);
+        }
         // ------------------------------------------------------------------ L sweep
         uint32_t syn0 = 0, syn1 = 0;
         static_for_down<n, 1>([&](auto S) {
@@ -832,6 +877,13 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
         });
         // ------------------------------------------------------------------ CRC early stop
         syn0 = __reduce_xor_sync(0xffffffffu, syn0);
+        if constexpr (DEFER) {
+            if ((t & 31) == 0) synp[(it & 1) * 2 * NW + (t >> 5)] = syn0;
+            ++it;
+            ++itc[0];
+            pending = true;
+            continue;  // read and decided after the next iteration's first exchange barrier
+        }
         if constexpr (FPT == 2 && !syn_packed) syn1 = __reduce_xor_sync(0xffffffffu, syn1);
         if constexpr (NW > 1) {
             uint32_t* sp = synp + (it & 1) * 2 * NW;
