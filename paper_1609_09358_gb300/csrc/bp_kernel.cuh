@@ -673,9 +673,10 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
     // before the stop decision; if the frame stops they are dropped.  They write only R[2..SC]
     // and the exchange buffer, and the outputs read L[1], R[1], R[n] and L[n+1] (SC < n).
     constexpr int SC = first_rcross<P>();
-    // (Not in the mixed kernel, whose many plans would spill more with it.)
+    // (Not in the mixed kernel, whose many plans would spill more with it, and not in the exact-g
+    // kernel at N = 4096, measured 4% slower with it.)
     constexpr bool DEFER = FPT == 1 && !WEIGHTED && !REENC && NW > 1 && SC > 0 && SC < n &&
-                           std::is_same<Src, CounterSource>::value;
+                           !(EXACT && n == 12) && std::is_same<Src, CounterSource>::value;
     bool pending = false;  // DEFER: an iteration's partial syndromes are written, not yet read
     int it = 0;  // iterations run by this group (selects the partial-syndrome slot parity)
     for (;;) {
