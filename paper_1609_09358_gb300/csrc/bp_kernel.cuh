@@ -52,7 +52,7 @@ struct BPPlan {
     // 1, 2, 4, 8, 16 modulo 32 in some order -- for group 1 that takes node bits 0, 1, 2, 8, 9
     // (a search over the plans finds such bits for N >= 1024 with b = 3 only).  The other plans
     // keep an XOR swizzle of index bits 5..7 into the bank bits (one XOR per access).
-    static constexpr bool PAD = (LOGR == 3 && LOGN >= 10) || (LOGR == 4 && LOGN == 10);
+    static constexpr bool PAD = (LOGR == 3 && LOGN >= 10) || (LOGR == 4 && LOGN >= 10);
     // node bit receiving thread-index bit q in group g: the non-window bits in ascending order,
     // except that group 1 of a PAD plan puts lane bits 3, 4 on node bits 8, 9 (b = 3) or lane
     // bit 4 on node bit 9 (b = 4, N = 1024)
@@ -60,8 +60,8 @@ struct BPPlan {
     {
         if (PAD && LOGR == 3 && g == 1)  // window 3..5: thread bits -> node bits 0 1 2 8 9 6 7 10 ...
             return q < 3 ? q : q < 5 ? q + 5 : q < 7 ? q + 1 : q + 3;
-        if (PAD && LOGR == 4 && g == 1)  // window 4..7: thread bits -> node bits 0 1 2 3 9 8
-            return q < 4 ? q : q == 4 ? 9 : 8;
+        if (PAD && LOGR == 4 && g == 1)  // window 4..7: thread bits -> node bits 0 1 2 3 9 8 10 11
+            return q < 4 ? q : q == 4 ? 9 : q == 5 ? 8 : q + 4;
         return q < win(g) ? q : q + LOGR;
     }
     // node bits from the thread index t (group g) and from the register index k
@@ -398,9 +398,9 @@ __host__ __device__ constexpr int first_rcross()
     return 0;
 }
 
-// Plan and frame groups per CTA of a kernel: the plain min-sum kernels at N = 1024 take 16 nodes
-// per thread (64 threads per frame, 4 column exchanges per iteration instead of 6), the others
-// the length's plan.
+// Plan and frame groups per CTA of a kernel: the plain min-sum kernels at N = 1024 and 4096 take
+// 16 nodes per thread (64 / 256 threads per frame, 4 column exchanges per iteration instead of 6),
+// the others the length's plan (the exact-g kernel at N = 4096 measured 11% slower with 16).
 template <int LOGN, int WEIGHTED, int VAR>
 struct BPKernelPlan {
     using Plan = typename BPConfig<LOGN>::Plan;
@@ -409,6 +409,11 @@ struct BPKernelPlan {
 template <>
 struct BPKernelPlan<10, 0, 0> {
     using Plan = BPPlan<10, 4>;
+    static constexpr int F = 1;
+};
+template <>
+struct BPKernelPlan<12, 0, 0> {
+    using Plan = BPPlan<12, 4>;
     static constexpr int F = 1;
 };
 

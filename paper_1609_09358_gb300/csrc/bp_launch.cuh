@@ -92,11 +92,11 @@ BPKernelInfo bp_kernel_info_var_t(int logn)
 {
     auto pick = [&](auto LOGN_C) -> BPKernelInfo {
         constexpr int LOGN = decltype(LOGN_C)::value;
-        using Cfg = BPConfig<LOGN>;
-        using P = typename Cfg::Plan;
-        constexpr int TH = Cfg::F * P::T;
-        const size_t smem = (size_t)Cfg::F * bp_slot_words<P>() * 4;
-        return {(const void*)bp_kernel<LOGN, float, 0, TH, false, VAR>, TH, smem, Cfg::F};
+        using KP = BPKernelPlan<LOGN, 0, VAR>;
+        using P = typename KP::Plan;
+        constexpr int TH = KP::F * P::T;
+        const size_t smem = (size_t)KP::F * bp_slot_words<P>() * 4;
+        return {(const void*)bp_kernel<LOGN, float, 0, TH, false, VAR>, TH, smem, KP::F};
     };
     switch (logn) {
         case 7: return pick(std::integral_constant<int, 7>{});
