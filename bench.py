@@ -195,6 +195,18 @@ def oracle_sample_rate(n_frames: int, ebn0: float, seed: int, min_seconds: float
             "fer": errs / done}
 
 
+def oracle_one_core(ebn0: float, seed: int, min_seconds: float = 5.0):
+    """The same oracle leg on one host thread (then all threads again)."""
+    import oracle
+    cores = oracle.num_threads()
+    oracle.set_threads(1)
+    try:
+        r = oracle_sample_rate(64, ebn0, seed, min_seconds=min_seconds)
+    finally:
+        oracle.set_threads(cores)
+    return {"value": r["value"], "unit": "Gbit/s", "cores": 1, "frames": r["frames"], "seconds": r["seconds"]}
+
+
 def run_reference(a, world, rank):
     if rank != 0:
         return 0
@@ -399,6 +411,7 @@ def main():
         line["cpu_baseline"] = {"value": r["value"], "unit": "Gbit/s", "cores": r["cores"], "kind": "oracle",
                                 "sample": "%d seeded frames of the same workload (%.1f s), C oracle, OpenMP"
                                           % (r["frames"], r["seconds"])}
+        line["cpu_baseline"]["one_core"] = oracle_one_core(a.ebn0, SEED + 98)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -38,3 +38,13 @@ def test_statistics_ranges_are_distinct():
         assert a + n <= b
     assert spans[0][0] >= 1 << 32
     assert bench.STATS_SEED != bench.SEED
+
+
+def test_oracle_one_core_leg_restores_threads():
+    """The one-thread oracle timing reports one core and leaves the oracle's thread count as it
+    found it (the all-cores leg and the reference arm run after it)."""
+    oracle = pytest.importorskip("oracle")
+    before = oracle.num_threads()
+    r = bench.oracle_one_core(2.5, bench.SEED + 98, min_seconds=0.0)
+    assert r["cores"] == 1 and r["frames"] == 64 and r["value"] > 0
+    assert oracle.num_threads() == before
