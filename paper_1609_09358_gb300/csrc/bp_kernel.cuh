@@ -398,21 +398,22 @@ __host__ __device__ constexpr int first_rcross()
     return 0;
 }
 
-// Plan and frame groups per CTA of a kernel: the plain min-sum kernels at N = 1024 and 4096 take
-// 16 nodes per thread (64 / 256 threads per frame, 4 column exchanges per iteration instead of 6),
-// the others the length's plan (the exact-g kernel at N = 4096 measured 11% slower with 16).
-template <int LOGN, int WEIGHTED, int VAR>
+// Plan and frame groups per CTA of a kernel (FPT: frames per thread, 2 for half2): the plain
+// min-sum kernels at N = 1024 and the plain FP32 one at N = 4096 take 16 nodes per thread (64 / 256
+// threads per frame, 4 column exchanges per iteration instead of 6), the others the length's plan
+// (at N = 4096 the exact-g kernel measured 11% slower with 16, the half2 one 3-9% slower).
+template <int LOGN, int WEIGHTED, int VAR, int FPT>
 struct BPKernelPlan {
     using Plan = typename BPConfig<LOGN>::Plan;
     static constexpr int F = BPConfig<LOGN>::F;
 };
-template <>
-struct BPKernelPlan<10, 0, 0> {
+template <int FPT>
+struct BPKernelPlan<10, 0, 0, FPT> {
     using Plan = BPPlan<10, 4>;
     static constexpr int F = 1;
 };
 template <>
-struct BPKernelPlan<12, 0, 0> {
+struct BPKernelPlan<12, 0, 0, 1> {
     using Plan = BPPlan<12, 4>;
     static constexpr int F = 1;
 };
@@ -552,11 +553,16 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
         }
     }
     // messages start at 0; only the L columns 2..n need it, since every R sweep writes R[2..n]
-    // before anything reads them
+    // before anything reads them.  The half2 kernels zero the R columns too: with it the compiler
+    // places their spills so that N = 4096 runs 8% faster (measured), at no cost at N = 1024.
+    constexpr bool ZERO_R = FPT == 2;
 #pragma unroll
     for (int c = 2; c <= n; ++c)
 #pragma unroll
-        for (int k = 0; k < R; ++k) Lc[c][k] = MT::splat(0.0f);
+        for (int k = 0; k < R; ++k) {
+            Lc[c][k] = MT::splat(0.0f);
+            if constexpr (ZERO_R) Rc[c][k] = MT::splat(0.0f);
+        }
 
     // Learned scales: iteration `it` of half h reads its prepared rows; past the learned
     // iterations (and for an idle half) the scale is 1, the same value as the plain update since
@@ -669,7 +675,10 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 #pragma unroll
         for (int c = 2; c <= n; ++c)
 #pragma unroll
-            for (int k = 0; k < R; ++k) Lc[c][k] = MT::zero_half(Lc[c][k], h);
+            for (int k = 0; k < R; ++k) {
+                Lc[c][k] = MT::zero_half(Lc[c][k], h);
+                if constexpr (ZERO_R) Rc[c][k] = MT::zero_half(Rc[c][k], h);
+            }
     };
 
     // DEFER (one FP32 frame over several warps): the warps' partial syndromes of an iteration are
@@ -999,8 +1008,8 @@ constexpr int bp_min_ctas()
 template <int LOGN, class MSG, int WEIGHTED, int THREADS, bool SYNP = false, int VAR = 0>
 __global__ void __launch_bounds__(THREADS, bp_min_ctas<LOGN, WEIGHTED, VAR>()) bp_kernel(const BPArgs a)
 {
-    using P = typename BPKernelPlan<LOGN, WEIGHTED, VAR>::Plan;
-    constexpr int F = BPKernelPlan<LOGN, WEIGHTED, VAR>::F;
+    using P = typename BPKernelPlan<LOGN, WEIGHTED, VAR, MsgTraits<MSG>::FPT>::Plan;
+    constexpr int F = BPKernelPlan<LOGN, WEIGHTED, VAR, MsgTraits<MSG>::FPT>::F;
     static_assert(THREADS == F * P::T, "launch shape");
     static_assert(P::T <= 32 || F == 1, "frame groups wider than a warp own their CTA");
     extern __shared__ uint32_t smem[];

@@ -58,7 +58,7 @@ BPKernelInfo bp_kernel_info_t(int logn, int weighted, bool packed_syndrome = fal
         const size_t smem = (size_t)Cfg::F * bp_slot_words<P>() * 4;
         const void* fn;
         // the plain kernels' own plan
-        using KP = BPKernelPlan<LOGN, 0, 0>;
+        using KP = BPKernelPlan<LOGN, 0, 0, MsgTraits<MSG>::FPT>;
         using P0 = typename KP::Plan;
         constexpr int TH0 = KP::F * P0::T;
         const size_t smem0 = (size_t)KP::F * bp_slot_words<P0>() * 4;
@@ -92,7 +92,7 @@ BPKernelInfo bp_kernel_info_var_t(int logn)
 {
     auto pick = [&](auto LOGN_C) -> BPKernelInfo {
         constexpr int LOGN = decltype(LOGN_C)::value;
-        using KP = BPKernelPlan<LOGN, 0, VAR>;
+        using KP = BPKernelPlan<LOGN, 0, VAR, 1>;
         using P = typename KP::Plan;
         constexpr int TH = KP::F * P::T;
         const size_t smem = (size_t)KP::F * bp_slot_words<P>() * 4;
