@@ -343,13 +343,24 @@ def main():
     # every step decodes the same frames: total algorithmic ops of the timed BP launches over their
     # summed device time (= ops per launch / average launch time when a step is one launch)
     achieved = ops_per_frame_iter * float(iters.sum()) * a.steps / (bp_ms * 1e-3)
-    traffic = None
+    traffic, pipes = None, None
+    ptag = "fp16" if prec == api.POLAR_FP16 else "fp32"
     tfile = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if os.path.exists(tfile):
         for line in open(tfile):
             f = line.split()
-            if len(f) >= 3 and f[0] == "bp_kernel" and f[1] == ("fp16" if prec == api.POLAR_FP16 else "fp32"):
+            if len(f) >= 3 and f[0] == "bp_kernel" and f[1] == ptag:
                 traffic = float(f[2])
+            if len(f) >= 3 and f[0] == "bp_kernel_pipes" and f[1] == ptag:
+                pipes = {kv.split("=")[0]: float(kv.split("=")[1]) for kv in f[2:]}
+    # HBM side of the same launches: algorithmic bytes (LLRs in, payload bits, status and iteration
+    # count out) and the ncu-measured traffic, over the average launch time, against the measured
+    # copy bandwidth
+    hbm_peak = float(peaks.get("hbm_gbs", 6790.0))
+    alg_bytes = B * (4 * N + (P + 7) // 8 + 3)
+    hbm = {"alg_gbs": alg_bytes / (bp_avg_ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+           "alg_frac": alg_bytes / (bp_avg_ms * 1e-3) / 1e9 / hbm_peak,
+           "traffic_gbs": traffic / (bp_avg_ms * 1e-3) / 1e9 if traffic else None}
     # a count that takes g and clip as two operations each gives 10 per PE half-iteration; on
     # sm_103a each is one min.xorsign.abs, so the 6-operation count against 128 lanes per SM per
     # clock is the same bound as the 3 comparisons per PE half-iteration against the comparison
@@ -362,7 +373,8 @@ def main():
                               "half-iteration = 3 comparison-pipe instructions at half rate" % (sms, lanes, sm_max_mhz),
                 "frac_10op": achieved * ops10 / ops_per_frame_iter / peak_ops,
                 "ops10_basis": "10 n N + K ops per frame-iteration (g and clip counted as 2 ops each) "
-                               "against the same peak"}
+                               "against the same peak",
+                "hbm": hbm, "ncu_pipes_pct": pipes}
 
     line = {"metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
