@@ -50,12 +50,13 @@ struct BPPlan {
     // compile-time offsets (no address arithmetic per access), and it is bank-conflict free when
     // in every group the 5 lane bits of the thread index land on node bits whose addresses are
     // 1, 2, 4, 8, 16 modulo 32 in some order -- for group 1 that takes node bits 0, 1, 2, 8, 9
-    // (a search over the plans finds such bits for N >= 1024 with b = 3 only).  The other plans
+    // with b = 3, and 0, 1, 2, 3, 9 with b = 4 (a search over the plans finds such bits for
+    // N >= 1024 with b = 3 and b = 4 only).  The other plans
     // keep an XOR swizzle of index bits 5..7 into the bank bits (one XOR per access).
     static constexpr bool PAD = (LOGR == 3 && LOGN >= 10) || (LOGR == 4 && LOGN >= 10);
     // node bit receiving thread-index bit q in group g: the non-window bits in ascending order,
     // except that group 1 of a PAD plan puts lane bits 3, 4 on node bits 8, 9 (b = 3) or lane
-    // bit 4 on node bit 9 (b = 4, N = 1024)
+    // bit 4 on node bit 9 (b = 4)
     __host__ __device__ static constexpr int tbit(int g, int q)
     {
         if (PAD && LOGR == 3 && g == 1)  // window 3..5: thread bits -> node bits 0 1 2 8 9 6 7 10 ...
@@ -661,8 +662,8 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
         }
     };
 
-    // replace the frame of half h by the next one: channel column and zeroed L messages (the R
-    // columns are rewritten by the next R sweep before they are read)
+    // replace the frame of half h by the next one: channel column and zeroed L messages (R too
+    // where ZERO_R; the next R sweep rewrites them before it reads them)
     auto refill = [&](int h) {
         fr[h] = fetch();
         itc[h] = 0;
