@@ -92,6 +92,26 @@ def test_bp_fp16_bit_exact_vs_binary16_emulation(N, K, crc, ebn0, B, imax):
     assert_bp_equal(got, ref, ocode)
 
 
+@pytest.mark.parametrize("N,K,crc,B", [(512, 256, 16, 40), (1024, 512, 16, 33), (1024, 512, 24, 17),
+                                       (2048, 1024, 24, 9), (4096, 2048, 16, 5)])
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_bp_fixed_iterations_bit_exact(N, K, crc, B, precision):
+    """Exactly T iterations whatever the CRC says (POLAR_FIXED_ITERS): every output after the
+    last one equals the oracle's BP without early stop.  With FP32 frames over several warps the
+    kernels read an iteration's stop decision one exchange later (after the next iteration's first
+    stages), and the 16-node plans (N = 1024, FP32 at 4096) exchange columns in three groups: both
+    must leave the T-th iteration's messages as they are."""
+    T = 7
+    ocode = fr.oracle_code(N, K, crc)
+    _, llr = fr.frames(ocode, 2.0, B, seed=4100 + N + K)
+    m = 20.0 if precision == "f32" else 32.0
+    ref = oracle.bp_decode(llr, ocode, T, m, precision, early_stop=False)
+    flag = api.POLAR_FP32 if precision == "f32" else api.POLAR_FP16
+    got = run_bp(ocode, llr, T, m, flag | api.POLAR_FIXED_ITERS)
+    assert np.all(got["iters"] == T)
+    assert_bp_equal(got, ref, ocode)
+
+
 @pytest.mark.parametrize("N,K,crc", [(128, 64, 8), (256, 128, 16), (512, 256, 16), (1024, 512, 16),
                                      (2048, 1024, 24)])
 @pytest.mark.parametrize("precision", ["f32", "f16"])
