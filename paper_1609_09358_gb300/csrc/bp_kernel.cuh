@@ -423,8 +423,9 @@ template <class P>
 __host__ __device__ constexpr int bp_slot_words()
 {
     // exchange buffers [2][XW] | syndrome columns, thread-major [R][T] | partial syndromes
-    // [2][2][NW] | packed payload bits [2][N/32] | fetched frame index [4]
-    return 2 * P::XW + P::N + 4 * P::NW + 2 * (P::N / 32) + 4;
+    // [2][2][NW] | packed payload bits [2][N/32] | fetched frame index [4] | at N = 4096 the
+    // channel column [XW], in the last group's exchange layout
+    return 2 * P::XW + P::N + 4 * P::NW + 2 * (P::N / 32) + 4 + (P::LOGN == 12 ? P::XW : 0);
 }
 
 // One frame group of T threads decoding frames from `src` until it runs dry.  Group `slot` of
@@ -511,6 +512,12 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
     uint32_t* synp = csyn + N;                             // [2 parity][2 frame][NW]
     uint32_t* pbits = synp + 4 * NW;                       // [2 frame][N/32]
     int* fetched = reinterpret_cast<int*>(pbits + 2 * (N / 32));
+    // CHS (N = 4096): the channel column lives in shared memory and is read into registers at the
+    // two stages that use it (stage n of each sweep) and by the outputs, so that its R registers
+    // are free for the rest of the iteration (the N = 4096 kernels run at the register file's
+    // limit).  Each thread reads back only the nodes it wrote: no barrier.
+    constexpr bool CHS = n == 12;
+    MSG* chs = reinterpret_cast<MSG*>(fetched + 4);
 
     // Frames of this group: half h (h < FPT) decodes frame fr[h]; when it stops it fetches the
     // next frame from the source.
@@ -525,6 +532,12 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 
     MSG Lc[n + 2][R];
     MSG Rc[n + 2][R];
+    auto chan_reload = [&]() {
+        if constexpr (CHS) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) Lc[n + 1][k] = xget<P, NG - 1>(chs, xbase, t, k);
+        }
+    };
     // SYNP, half2: both frames' syndromes share one word (frame 0 in the low half, frame 1 in the
     // high half), the columns are stored doubled.  SYNP, FP32 pairs: registers k and k + 1 share
     // one column word (k's column low, k + 1's high), two such words per thread and uint2,
@@ -550,7 +563,11 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const int j = P::node(NG - 1, t, k);
-            Lc[n + 1][k] = MT::pair(y0 ? stage_clip(__ldg(y0 + j), M) : 0.0f, y1 ? stage_clip(__ldg(y1 + j), M) : 0.0f);
+            const MSG v = MT::pair(y0 ? stage_clip(__ldg(y0 + j), M) : 0.0f, y1 ? stage_clip(__ldg(y1 + j), M) : 0.0f);
+            if constexpr (CHS)
+                xput<P, NG - 1>(chs, xbase, t, k, v);
+            else
+                Lc[n + 1][k] = v;
         }
     }
     // messages start at 0; only the L columns 2..n need it, since every R sweep writes R[2..n]
@@ -641,6 +658,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
         }
         if (a.llr_x) {
             // R[n+1] of the last R sweep, recomputed from R[n] and the channel column
+            chan_reload();
             constexpr int q = n - 1, g = P::grp(q), dd = 1 << (q - P::win(g));
 #pragma unroll
             for (int k = 0; k < R; ++k) {
@@ -671,7 +689,10 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const float v = y ? stage_clip(__ldg(y + P::node(NG - 1, t, k)), M) : 0.0f;
-            Lc[n + 1][k] = MT::set_half(Lc[n + 1][k], v, h);
+            if constexpr (CHS)
+                xput<P, NG - 1>(chs, xbase, t, k, MT::set_half(xget<P, NG - 1>(chs, xbase, t, k), v, h));
+            else
+                Lc[n + 1][k] = MT::set_half(Lc[n + 1][k], v, h);
         }
 #pragma unroll
         for (int c = 2; c <= n; ++c)
@@ -706,6 +727,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             constexpr bool cross = P::rcross(s);
             MSG* xb = xbuf + (P::xidx_r(s) & 1) * P::XW;
             if constexpr (WEIGHTED) wn = last ? wload(1, n) : wload(0, s + 1);
+            if constexpr (last) chan_reload();
             // outputs of the PE (k, k2): R[s+1] registers, the exchange buffer, or (last stage) only
             // the re-encoding stop's hard decisions of LLR(x)
             auto emit = [&](int k, int k2, MSG o1, MSG o2) {
@@ -792,6 +814,7 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
             constexpr bool cross = P::lcross(s);
             MSG* xb = xbuf + (P::xidx_l(s) & 1) * P::XW;
             if constexpr (WEIGHTED && !first) wn = wload(1, s - 1);
+            if constexpr (s == n) chan_reload();
             auto emit = [&](int k, int k2, MSG o1, MSG o2) {
                 if constexpr (cross) {
                     xput<P, g>(xb, xbase, t, k, o1);
