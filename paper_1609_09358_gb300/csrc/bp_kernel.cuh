@@ -423,9 +423,9 @@ template <class P>
 __host__ __device__ constexpr int bp_slot_words()
 {
     // exchange buffers [2][XW] | syndrome columns, thread-major [R][T] | partial syndromes
-    // [2][2][NW] | packed payload bits [2][N/32] | fetched frame index [4] | at N = 4096 the
+    // [2][2][NW] | packed payload bits [2][N/32] | fetched frame index [4] | from N = 1024 on the
     // channel column [XW], in the last group's exchange layout
-    return 2 * P::XW + P::N + 4 * P::NW + 2 * (P::N / 32) + 4 + (P::LOGN == 12 ? P::XW : 0);
+    return 2 * P::XW + P::N + 4 * P::NW + 2 * (P::N / 32) + 4 + (P::LOGN >= 10 ? P::XW : 0);
 }
 
 // One frame group of T threads decoding frames from `src` until it runs dry.  Group `slot` of
@@ -512,11 +512,13 @@ __device__ __forceinline__ void bp_run_group(const BPArgs& a, const DevCode& C, 
     uint32_t* synp = csyn + N;                             // [2 parity][2 frame][NW]
     uint32_t* pbits = synp + 4 * NW;                       // [2 frame][N/32]
     int* fetched = reinterpret_cast<int*>(pbits + 2 * (N / 32));
-    // CHS (N = 4096): the channel column lives in shared memory and is read into registers at the
+    // CHS (N >= 1024): the channel column lives in shared memory and is read into registers at the
     // two stages that use it (stage n of each sweep) and by the outputs, so that its R registers
-    // are free for the rest of the iteration (the N = 4096 kernels run at the register file's
-    // limit).  Each thread reads back only the nodes it wrote: no barrier.
-    constexpr bool CHS = n == 12;
+    // are free for the rest of the iteration (the long kernels run at the register file's limit;
+    // measured: N = 4096 exact g 7% faster, half2 9%, N = 2048 learned 5%, N = 1024 FP32 1.6%).
+    // Each thread reads back only the nodes it wrote: no barrier.  Not for the plain and the
+    // aligned-pair half2 kernels at N = 1024 (3.4% and 0.2% slower with it).
+    constexpr bool CHS = n >= 11 || (n == 10 && (FPT == 1 || WEIGHTED == 1));
     MSG* chs = reinterpret_cast<MSG*>(fetched + 4);
 
     // Frames of this group: half h (h < FPT) decodes frame fr[h]; when it stops it fetches the
