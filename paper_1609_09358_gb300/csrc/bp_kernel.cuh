@@ -17,8 +17,9 @@
 // exactly in the bits of g's window, so b consecutive PE stages run entirely in registers.  At
 // a group boundary the boundary column is exchanged once through a swizzled shared-memory
 // buffer (bank-conflict free for every access of every plan, checked at compile time).  All
-// messages of all columns stay in registers for the frame's whole life; HBM is touched once to
-// read the channel LLRs and once to write the decided payload bits.
+// messages stay in registers for the frame's whole life (most kernels from N = 1024 on keep the
+// channel column, read at two stages per iteration, in shared memory instead: CHS below); HBM is
+// touched once to read the channel LLRs and once to write the decided payload bits.
 //
 // Storage of column c: R[c] lives in the mapping of stage c (the group that reads it), L[c] in
 // the mapping of stage c-1.  The clip of g(R[s][j], .) and g(L[s+1][j], .) is skipped when no
