@@ -92,6 +92,22 @@ def test_bp_fp16_bit_exact_vs_binary16_emulation(N, K, crc, ebn0, B, imax):
     assert_bp_equal(got, ref, ocode)
 
 
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+@pytest.mark.parametrize("N,K,crc,B", [(2048, 1024, 24, 1400), (4096, 2048, 16, 700)])
+def test_bp_refill_long_codes_bit_exact(N, K, crc, B, precision):
+    """Several frames per frame group at N = 2048 and 4096 (more frames than the persistent grid
+    holds), so every group refills: the channel column these kernels keep in shared memory is
+    rewritten per frame (per half of a half2 register), and every output must still equal the
+    oracle's."""
+    ocode = fr.oracle_code(N, K, crc)
+    _, llr = fr.frames(ocode, 3.0, B, seed=4700 + N)
+    m = 20.0 if precision == "f32" else 32.0
+    ref = oracle.bp_decode(llr, ocode, 50, m, precision)
+    flag = api.POLAR_FP32 if precision == "f32" else api.POLAR_FP16
+    got = run_bp(ocode, llr, 50, m, flag)
+    assert_bp_equal(got, ref, ocode)
+
+
 @pytest.mark.parametrize("N,K,crc,B", [(512, 256, 16, 40), (1024, 512, 16, 33), (1024, 512, 24, 17),
                                        (2048, 1024, 24, 9), (4096, 2048, 16, 5)])
 @pytest.mark.parametrize("precision", ["f32", "f16"])
