@@ -254,20 +254,26 @@ def test_decision_aided_scl_and_hybrid_bit_exact(N, K, crc, L, frac):
     assert np.array_equal(api.unpack_bits(bits.cpu().numpy(), ocode.P), oracle.payload_of(href["u_hat"], ocode))
 
 
-def test_bp_edge_inputs():
-    """NaN reads as an erasure, +-inf clips, max_iters = 1, a single frame."""
-    ocode = fr.oracle_code(256, 128, 16)
+@pytest.mark.parametrize("N,K", [(256, 128), (1024, 512), (4096, 2048)])
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_bp_edge_inputs(N, K, precision):
+    """NaN reads as an erasure, +-inf clips, max_iters = 1, a single frame; at N = 1024 and 4096
+    also through the kernels that keep the channel column in shared memory and (FP32) read the
+    stop decision one exchange late."""
+    ocode = fr.oracle_code(N, K, 16)
     _, llr = fr.frames(ocode, 2.0, 5, seed=5)
     llr[0, :7] = np.nan
     llr[1, ::3] = np.inf
     llr[2, ::5] = -np.inf
     llr[3] = 0.0
+    m = 20.0 if precision == "f32" else 32.0
+    flag = api.POLAR_FP32 if precision == "f32" else api.POLAR_FP16
     for imax in (1, 25):
-        ref = oracle.bp_decode(llr, ocode, imax, 20.0, "f32")
-        got = run_bp(ocode, llr, imax, 20.0)
+        ref = oracle.bp_decode(llr, ocode, imax, m, precision)
+        got = run_bp(ocode, llr, imax, m, flag)
         assert_bp_equal(got, ref, ocode)
-    ref = oracle.bp_decode(llr[:1], ocode, 25, 20.0, "f32")
-    assert_bp_equal(run_bp(ocode, llr[:1], 25, 20.0), ref, ocode)
+    ref = oracle.bp_decode(llr[:1], ocode, 25, m, precision)
+    assert_bp_equal(run_bp(ocode, llr[:1], 25, m, flag), ref, ocode)
 
 
 def test_bp_degenerate_codes():
