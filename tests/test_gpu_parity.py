@@ -300,6 +300,31 @@ def run_scl(ocode, llr, L):
     return api.unpack_bits(bits.cpu().numpy(), ocode.P), status.cpu().numpy()
 
 
+def _wilson(k, n, z=1.959963984540054):
+    p = k / n
+    c = (p + z * z / (2 * n)) / (1 + z * z / n)
+    h = z * np.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / (1 + z * z / n)
+    return c - h, c + h
+
+
+def test_scl_fer_non_increasing_in_list_size():
+    """A statistical property of CA-SCL: a larger list does not raise the frame-error rate.  On the
+    same 6000 frames (N = 512, K = 256, CRC-16, 1.5 dB) the errors for L = 1, 2, ..., 32 must not
+    grow beyond the 95% Wilson interval of the previous list size, and L = 32 must beat SC (L = 1)
+    outright.  (CRC false accepts grow with L, but at about L / 2^16 per frame they stay far below
+    these error rates.)"""
+    ocode = fr.oracle_code(512, 256, 16)
+    pay, llr = fr.frames_large(ocode, 1.5, 6000, seed=9100)
+    errs = []
+    for L in (1, 2, 4, 8, 16, 32):
+        bits, _ = run_scl(ocode, llr, L)
+        errs.append(int(np.sum(np.any(bits != pay, axis=1))))
+    n = llr.shape[0]
+    for a, b in zip(errs, errs[1:]):
+        assert b / n <= _wilson(a, n)[1], errs
+    assert _wilson(errs[-1], n)[1] < _wilson(errs[0], n)[0], errs
+
+
 SCL_CASES = [
     # N, K, crc, Eb/N0, B, L
     (128, 64, 8, 1.0, 50, 4),
