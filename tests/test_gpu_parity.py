@@ -384,6 +384,24 @@ def run_hybrid(ocode, llr, imax, L, llr_max=20.0, precision=api.POLAR_FP32):
             dec.iters.cpu().numpy().astype(np.int32), nfb)
 
 
+@pytest.mark.parametrize("ebn0", [1.5, 2.0])
+def test_hybrid_fer_matches_scl_alone(ebn0):
+    """Sec. IV: the hybrid decodes as well as CA-SCL alone.  On the same 20 000 frames (N = 1024,
+    K = 512, CRC-16, L = 8, i_max = 200) the two frame-error rates' 95% Wilson intervals overlap.
+    (BP tests the CRC after every iteration, so a few frames it gets wrong pass the CRC: the
+    hybrid's rate can only be a little higher.)"""
+    ocode = fr.oracle_code(1024, 512, 16)
+    pay, llr = fr.frames_large(ocode, ebn0, 20000, seed=9300 + int(10 * ebn0))
+    bh, _, _, _ = run_hybrid(ocode, llr, 200, 8)
+    bs, _ = run_scl(ocode, llr, 8)
+    n = llr.shape[0]
+    eh = int(np.sum(np.any(bh != pay, axis=1)))
+    es = int(np.sum(np.any(bs != pay, axis=1)))
+    lo_h, hi_h = _wilson(eh, n)
+    lo_s, hi_s = _wilson(es, n)
+    assert lo_h <= hi_s and lo_s <= hi_h, (eh, es)
+
+
 @pytest.mark.parametrize("N,K,crc,ebn0,B,imax,L", [
     (128, 64, 8, 2.5, 1000, 50, 4),   # the small plain-hybrid workload in full
     (128, 64, 8, 1.0, 300, 50, 4),
